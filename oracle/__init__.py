@@ -1,0 +1,395 @@
+"""CPU FP64 oracle for surface multigrid (Liu, Zhang, Ben-Chen, Jacobson 2021).
+
+TEST INFRASTRUCTURE ONLY.  Only `tests/`, `__graft_entry__.smoke()` and the
+CPU-baseline leg of `bench.py` may import this package.  The product library
+never calls it and shares no code with it: the only common inputs are the
+seeded meshes and vectors from `synth`, and the hierarchy of prolongations
+P_1..P_H, which the method's setup stage produces from geometry alone and
+which the oracle takes as given data (Alg. 1: P's are computed once, before
+A and b exist).
+
+What is computed, in the paper's order and notation:
+  * A = M + t L on the mesh (Sec. 6 "cotangent Laplacian"; lumped mass).  The
+    paper prints no formula: L is the positive semi-definite cotan Laplacian
+    (off-diagonal -(cot a + cot b)/2), M the barycentric lumped mass.
+  * Dirichlet reduction (App. "Dirichlet Boundary Conditions").
+  * Galerkin coarse operators A_{h+1} = P_{h+1}^T A_h P_{h+1} (Eq. "gca" with R = P^T).
+  * Greedy colouring (Alg. 3) and colour-ordered Gauss-Seidel (App. "Multi-Color
+    Gauss Seidel").
+  * The V-cycle of Alg. 2 and the solve loop of Alg. 1.
+  * The mixed-precision form: FP32 V-cycles inside FP64 iterative refinement.
+
+Pins (what fixes each function other than itself) live in tests/test_oracle_pins.py.
+Parity unpinned: none of the functions here; the convergence *rate* of the
+cycle has no printed value in the paper and is pinned only by rho < 1.
+"""
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import build as _build
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_greedy_colouring.argtypes = [i64, p, p, p]
+        lib.oracle_greedy_colouring.restype = i64
+        for name in ("oracle_gs_sweep_f64", "oracle_gs_sweep_f32"):
+            getattr(lib, name).argtypes = [i64, p, p, p, p, i64, p, p, i64]
+            getattr(lib, name).restype = i64
+        lib.oracle_cholesky.argtypes = [i64, p, p]
+        lib.oracle_cholesky.restype = i64
+        lib.oracle_chol_solve.argtypes = [i64, p, p, p, i64]
+        lib.oracle_chol_solve.restype = None
+        _LIB = lib
+    return _LIB
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------------------
+# Assembly: A = M + t L
+# ---------------------------------------------------------------------------
+def mesh_pattern(n, F):
+    """Structural 1-ring pattern of a mesh operator: every edge (both directions)
+    plus the diagonal, as a CSR matrix of ones with sorted column indices."""
+    F = np.asarray(F, dtype=np.int64)
+    r = np.concatenate([F[:, 0], F[:, 1], F[:, 1], F[:, 2], F[:, 2], F[:, 0], np.arange(n)])
+    c = np.concatenate([F[:, 1], F[:, 0], F[:, 2], F[:, 1], F[:, 0], F[:, 2], np.arange(n)])
+    S = sp.csr_matrix((np.ones(r.shape[0]), (r, c)), shape=(n, n))
+    S.sum_duplicates()
+    S.data[:] = 1.0
+    S.sort_indices()
+    return S
+
+
+def on_pattern(S, C):
+    """Values of C placed on the structural pattern S (pattern(C) must be a subset
+    of pattern(S)); entries of S absent from C are explicit zeros."""
+    S = S.tocsr()
+    S.sort_indices()
+    C = C.tocsr()
+    C.sum_duplicates()
+    ncol = S.shape[1]
+    rs = np.repeat(np.arange(S.shape[0], dtype=np.int64), np.diff(S.indptr))
+    rc = np.repeat(np.arange(C.shape[0], dtype=np.int64), np.diff(C.indptr))
+    ks = rs * ncol + S.indices
+    kc = rc * ncol + C.indices
+    pos = np.searchsorted(ks, kc)
+    if kc.size and (np.any(pos >= ks.size) or np.any(ks[np.minimum(pos, ks.size - 1)] != kc)):
+        raise ValueError("values outside the structural pattern")
+    data = np.zeros(ks.size, dtype=C.dtype)
+    data[pos] = C.data
+    return sp.csr_matrix((data, S.indices.copy(), S.indptr.copy()), shape=S.shape)
+
+
+def face_cotangents_areas(V, F):
+    """Per face (i, j, k): cot of the angle at each corner and the face area.
+    cot at corner a = (e1 . e2) / |e1 x e2| with e1, e2 the two edges leaving a."""
+    V = np.asarray(V, dtype=np.float64)
+    F = np.asarray(F, dtype=np.int64)
+    cots = np.zeros((F.shape[0], 3))
+    for c in range(3):
+        a = V[F[:, c]]
+        e1 = V[F[:, (c + 1) % 3]] - a
+        e2 = V[F[:, (c + 2) % 3]] - a
+        cots[:, c] = np.einsum("ij,ij->i", e1, e2) / np.linalg.norm(np.cross(e1, e2), axis=1)
+    area = 0.5 * np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1)
+    return cots, area
+
+
+def cotan_laplacian(V, F):
+    """PSD cotangent Laplacian: for each face and each corner k opposite edge (i, j),
+    L_ij = L_ji -= cot(k)/2 and L_ii, L_jj += cot(k)/2.  Hence L 1 = 0."""
+    n = np.asarray(V).shape[0]
+    F = np.asarray(F, dtype=np.int64)
+    cots, _ = face_cotangents_areas(V, F)
+    rows, cols, vals = [], [], []
+    for k in range(3):
+        i, j = F[:, (k + 1) % 3], F[:, (k + 2) % 3]
+        w = 0.5 * cots[:, k]
+        rows += [i, j, i, j]
+        cols += [j, i, i, j]
+        vals += [-w, -w, w, w]
+    L = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    return on_pattern(mesh_pattern(n, F), L)
+
+
+def lumped_mass(V, F):
+    """Barycentric lumped mass: M_ii = sum over faces at i of area / 3."""
+    n = np.asarray(V).shape[0]
+    F = np.asarray(F, dtype=np.int64)
+    _, area = face_cotangents_areas(V, F)
+    m = np.zeros(n)
+    for c in range(3):
+        np.add.at(m, F[:, c], area / 3.0)
+    return m
+
+
+def system_matrix(V, F, t):
+    """A = M + t L on the 1-ring pattern (CSR, sorted columns, diagonal present)."""
+    n = np.asarray(V).shape[0]
+    L = cotan_laplacian(V, F)
+    A = L * t + sp.diags(lumped_mass(V, F))
+    return on_pattern(mesh_pattern(n, F), A)
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet reduction (App. "Dirichlet Boundary Conditions")
+# ---------------------------------------------------------------------------
+def dirichlet_reduce(A, Ps, known):
+    """Reduce to the unknowns: A_uu, the rows P_{u:} of the finest prolongation with
+    all-zero columns removed, and the matching rows removed from the next P.
+    Returns (A_uu, [P_1', P_2', ...], unknown_index, kept_coarse_columns)."""
+    known = np.asarray(known, dtype=bool)
+    u = np.flatnonzero(~known)
+    A = A.tocsr()
+    Auu = A[u][:, u].tocsr()
+    Auu.sort_indices()
+    Ps = [P.tocsr() for P in Ps]
+    if not Ps:
+        return Auu, [], u, None
+    P1u = Ps[0][u].tocsr()
+    colmax = np.asarray(P1u.max(axis=0).todense()).ravel()
+    keep = np.flatnonzero(colmax > 0)
+    out = [P1u[:, keep].tocsr()]
+    if len(Ps) > 1:
+        out.append(Ps[1][keep].tocsr())
+        out += Ps[2:]
+    return Auu, out, u, keep
+
+
+# ---------------------------------------------------------------------------
+# Galerkin coarse operator (Eq. gca with R = P^T)
+# ---------------------------------------------------------------------------
+def galerkin_pattern(S, P):
+    """Structural pattern of P^T S P: products of non-negative 0/1 matrices never cancel."""
+    Pb = P.tocsr().copy()
+    Pb.data = np.ones_like(Pb.data)
+    Sb = S.tocsr().copy()
+    Sb.data = np.ones_like(Sb.data)
+    C = (Pb.T @ Sb @ Pb).tocsr()
+    C.data[:] = 1.0
+    C.sort_indices()
+    return C
+
+
+def galerkin(A, P):
+    """A_c = P^T A P, values on the structural pattern of P^T A P."""
+    C = (P.T.tocsr() @ A.tocsr() @ P.tocsr()).tocsr()
+    return on_pattern(galerkin_pattern(A, P), C)
+
+
+# ---------------------------------------------------------------------------
+# Colouring (Alg. 3) and Gauss-Seidel
+# ---------------------------------------------------------------------------
+def greedy_colouring(S):
+    """Colours of the off-diagonal graph of pattern S by Alg. 3 (C loop)."""
+    S = S.tocsr()
+    S.sort_indices()
+    n = S.shape[0]
+    rp = S.indptr.astype(np.int64)
+    ci = S.indices.astype(np.int64)
+    colour = np.empty(n, dtype=np.int32)
+    k = _lib().oracle_greedy_colouring(n, _ptr(rp), _ptr(ci), _ptr(colour))
+    if k < 0:
+        raise MemoryError("colouring failed")
+    return colour
+
+
+def colour_order(colour, reverse=False):
+    """Row order of a sweep: colour classes one after another (ascending colour
+    ids, or descending when reverse), rows ascending within a class."""
+    colour = np.asarray(colour)
+    key = -colour if reverse else colour
+    return np.lexsort((np.arange(colour.size), key)).astype(np.int64)
+
+
+def gs_sweep(A, x, b, order):
+    """One Gauss-Seidel pass over `order`; x (n or n x k) is updated in place."""
+    A = A.tocsr()
+    dt = A.dtype
+    fn = _lib().oracle_gs_sweep_f64 if dt == np.float64 else _lib().oracle_gs_sweep_f32
+    rp = A.indptr.astype(np.int64)
+    ci = A.indices.astype(np.int64)
+    val = np.ascontiguousarray(A.data)
+    xb = x.reshape(x.shape[0], -1)
+    bb = np.ascontiguousarray(b.reshape(b.shape[0], -1), dtype=dt)
+    assert xb.flags.c_contiguous and xb.dtype == dt
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    st = fn(A.shape[0], _ptr(rp), _ptr(ci), _ptr(val), _ptr(order), order.size,
+            _ptr(bb), _ptr(xb), xb.shape[1])
+    if st != 0:
+        raise ZeroDivisionError("zero diagonal in row %d" % (-st - 1))
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Dense Cholesky of the coarsest operator
+# ---------------------------------------------------------------------------
+def cholesky(Ad):
+    Ad = np.ascontiguousarray(Ad, dtype=np.float64)
+    n = Ad.shape[0]
+    L = np.empty_like(Ad)
+    st = _lib().oracle_cholesky(n, _ptr(Ad), _ptr(L))
+    if st != 0:
+        raise np.linalg.LinAlgError("not SPD: pivot %d" % (-st - 1))
+    return L
+
+
+def chol_solve(L, b):
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    bb = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(L.shape[0], -1))
+    x = np.empty_like(bb)
+    _lib().oracle_chol_solve(L.shape[0], _ptr(L), _ptr(bb), _ptr(x), bb.shape[1])
+    return x.reshape(np.shape(b))
+
+
+# ---------------------------------------------------------------------------
+# Hierarchy, V-cycle (Alg. 2) and solve loop (Alg. 1)
+# ---------------------------------------------------------------------------
+@dataclass
+class Level:
+    A: sp.csr_matrix                 # A_h
+    P: sp.csr_matrix = None          # P_{h+1}: n_h x n_{h+1} (None at the coarsest)
+    colour: np.ndarray = None
+    fwd: np.ndarray = None           # colour-major sweep order
+    rev: np.ndarray = None           # reversed colour classes
+    L: np.ndarray = None             # Cholesky factor (coarsest only)
+    A32: sp.csr_matrix = None
+    P32: sp.csr_matrix = None
+
+
+@dataclass
+class Options:
+    mu_pre: int = 2
+    mu_post: int = 2
+    post_reverse: bool = True        # post-relaxation visits the colour classes in reverse
+    rtol: float = 1e-10
+    max_cycles: int = 100
+
+
+def build_levels(A0, Ps):
+    """Levels 0..H from A_0 and P_1..P_H: Galerkin products, colourings, the
+    Cholesky factor of A_H."""
+    levels = []
+    A = A0.tocsr()
+    A.sort_indices()
+    for P in Ps:
+        col = greedy_colouring(A)
+        levels.append(Level(A=A, P=P.tocsr(), colour=col, fwd=colour_order(col),
+                            rev=colour_order(col, reverse=True)))
+        A = galerkin(A, P)
+    levels.append(Level(A=A, L=cholesky(A.toarray())))
+    for lv in levels:
+        lv.A32 = lv.A.astype(np.float32)
+        if lv.P is not None:
+            lv.P32 = lv.P.astype(np.float32)
+    return levels
+
+
+def relax(lv, x, b, sweeps, reverse, single=False):
+    A = lv.A32 if single else lv.A
+    for _ in range(sweeps):
+        gs_sweep(A, x, b, lv.rev if reverse else lv.fwd)
+    return x
+
+
+def vcycle(levels, h, x, b, opt, single=False):
+    """Alg. 2.  x_old is updated and returned.  Coarser levels start from 0.
+    Reading of the update step: the correction is added to the pre-relaxed
+    iterate x_old' (the printed x_old would discard the pre-relaxation)."""
+    lv = levels[h]
+    if h == len(levels) - 1:
+        if single:                   # coarsest factor stays in FP64
+            return chol_solve(lv.L, b.astype(np.float64)).astype(np.float32)
+        return chol_solve(lv.L, b)
+    A = lv.A32 if single else lv.A
+    P = lv.P32 if single else lv.P
+    x = relax(lv, x, b, opt.mu_pre, False, single)                    # pre-relaxation
+    r = P.T @ (b - A @ x)                                             # restrict residual
+    nc = levels[h + 1].A.shape[0]
+    zero = np.zeros((nc,) + b.shape[1:], dtype=b.dtype)
+    c = vcycle(levels, h + 1, zero, r, opt, single)                   # coarse correction
+    x = x + P @ c                                                     # prolong and add
+    x = np.ascontiguousarray(x)
+    x = relax(lv, x, b, opt.mu_post, opt.post_reverse, single)        # post-relaxation
+    return x
+
+
+def rel_residual(A, x, b):
+    """max over right-hand sides of ||b - A x||_2 / ||b||_2 (absolute when b = 0)."""
+    r = (b - A @ x).reshape(b.shape[0], -1)
+    bn = np.linalg.norm(b.reshape(b.shape[0], -1), axis=0)
+    rn = np.linalg.norm(r, axis=0)
+    return float(np.max(np.where(bn > 0, rn / np.where(bn > 0, bn, 1.0), rn)))
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    cycles: int
+    history: list = field(default_factory=list)    # relative residual before cycle 1, after each cycle
+    iterates: list = field(default_factory=list)
+
+
+def solve(levels, b, x0=None, opt=None, keep_iterates=False):
+    """Alg. 1: repeat V-cycles while the relative residual exceeds rtol."""
+    opt = opt or Options()
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    A = levels[0].A
+    hist = [rel_residual(A, x, b)]
+    its = []
+    k = 0
+    while hist[-1] > opt.rtol and k < opt.max_cycles:
+        x = vcycle(levels, 0, x, b, opt)
+        k += 1
+        hist.append(rel_residual(A, x, b))
+        if keep_iterates:
+            its.append(x.copy())
+        if not np.isfinite(hist[-1]):
+            break
+    return SolveResult(x=x, cycles=k, history=hist, iterates=its)
+
+
+def solve_mixed(levels, b, x0=None, opt=None, keep_iterates=False):
+    """Mixed precision: x_{k+1} = x_k + Vcycle_FP32(b - A x_k), with the residual and
+    the update in FP64 and the coarsest Cholesky in FP64."""
+    opt = opt or Options()
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    A = levels[0].A
+    hist = [rel_residual(A, x, b)]
+    its = []
+    k = 0
+    while hist[-1] > opt.rtol and k < opt.max_cycles:
+        r = (b - A @ x).astype(np.float32)
+        d = vcycle(levels, 0, np.zeros_like(r), r, opt, single=True)
+        x = x + d.astype(np.float64)
+        k += 1
+        hist.append(rel_residual(A, x, b))
+        if keep_iterates:
+            its.append(x.copy())
+        if not np.isfinite(hist[-1]):
+            break
+    return SolveResult(x=x, cycles=k, history=hist, iterates=its)
+
+
+def convergence_factor(history):
+    """rho = (r_k / r_0)^(1/k) over the recorded cycles."""
+    k = len(history) - 1
+    if k <= 0 or history[0] == 0:
+        return 0.0
+    return float((history[-1] / history[0]) ** (1.0 / k))

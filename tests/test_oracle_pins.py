@@ -1,0 +1,278 @@
+"""Pins of the oracle to facts fixed outside it: closed forms, identities,
+textbook special cases, a hand-worked run of Alg. 3 and independent library
+routines.  A dropped term, a sign or index error, or a transposed operand in
+the oracle fails at least one of these."""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# assembly
+# ---------------------------------------------------------------------------
+def test_laplacian_annihilates_constants_and_is_symmetric():
+    V, F = synth.perturbed_icosphere(3, seed=3)
+    L = oracle.cotan_laplacian(V, F)
+    assert abs(L - L.T).max() == 0.0
+    scale = abs(L).max()
+    assert np.abs(L @ np.ones(V.shape[0])).max() < 1e-12 * scale
+
+
+def _dirichlet_energy(V, F, f):
+    """sum_T area_T |grad f_T|^2 with grad phi_c = n x e_c / (2 area), e_c the edge
+    opposite corner c taken counter-clockwise: the gradient form, not cotangents."""
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    nrm = np.cross(b - a, c - a)
+    dbl = np.linalg.norm(nrm, axis=1)
+    nh = nrm / dbl[:, None]
+    g = np.zeros_like(a)
+    for k, e in ((0, c - b), (1, a - c), (2, b - a)):
+        g += f[F[:, k]][:, None] * np.cross(nh, e) / dbl[:, None]
+    return float(np.sum(0.5 * dbl * np.einsum("ij,ij->i", g, g)))
+
+
+def test_laplacian_quadratic_form_is_dirichlet_energy():
+    V, F = synth.perturbed_icosphere(3, seed=5)
+    rng = np.random.default_rng(0)
+    L = oracle.cotan_laplacian(V, F)
+    for _ in range(3):
+        f = rng.standard_normal(V.shape[0])
+        e = _dirichlet_energy(V, F, f)
+        assert abs(f @ (L @ f) - e) < 1e-11 * e
+
+
+def test_right_triangle_grid_gives_five_point_stencil():
+    N = 9
+    g = np.arange(N, dtype=float)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    V = np.stack([X.ravel(), Y.ravel(), np.zeros(N * N)], 1)
+    F = []
+    for a in range(N - 1):
+        for b in range(N - 1):
+            v00, v10, v11, v01 = a * N + b, (a + 1) * N + b, (a + 1) * N + b + 1, a * N + b + 1
+            F += [(v00, v10, v11), (v00, v11, v01)]
+    L = oracle.cotan_laplacian(V, np.array(F)).toarray()
+    for a in range(1, N - 1):
+        for b in range(1, N - 1):
+            i = a * N + b
+            expect = np.zeros(N * N)
+            expect[i] = 4.0
+            for j in (i - 1, i + 1, i - N, i + N):
+                expect[j] = -1.0
+            assert np.allclose(L[i], expect, atol=1e-14)
+
+
+def test_laplacian_linear_precision_on_planar_disk():
+    V, F, bnd = synth.disk(24, jitter=0.05, seed=2)
+    L = oracle.cotan_laplacian(V, F)
+    for k in range(2):
+        r = L @ V[:, k]
+        assert np.abs(r[~bnd]).max() < 1e-12
+
+
+def test_lumped_mass_sums_to_area():
+    V, F = synth.perturbed_icosphere(3, seed=1)
+    m = oracle.lumped_mass(V, F)
+    # Heron's formula, independent of the cross product used by the oracle
+    la = np.linalg.norm(V[F[:, 1]] - V[F[:, 2]], axis=1)
+    lb = np.linalg.norm(V[F[:, 2]] - V[F[:, 0]], axis=1)
+    lc = np.linalg.norm(V[F[:, 0]] - V[F[:, 1]], axis=1)
+    s = 0.5 * (la + lb + lc)
+    heron = np.sqrt(s * (s - la) * (s - lb) * (s - lc))
+    assert np.all(m > 0)
+    assert abs(m.sum() - heron.sum()) < 1e-12 * heron.sum()
+    V6, F6 = synth.icosphere(6)
+    assert abs(oracle.lumped_mass(V6, F6).sum() - 4 * np.pi) < 2e-3 * 4 * np.pi
+
+
+def test_system_matrix_is_spd_with_mesh_pattern():
+    V, F = synth.perturbed_icosphere(2, seed=0)
+    A = oracle.system_matrix(V, F, 1e-2)
+    S = oracle.mesh_pattern(V.shape[0], F)
+    assert (A.indptr == S.indptr).all() and (A.indices == S.indices).all()
+    Ad = A.toarray()
+    assert np.linalg.eigvalsh(Ad).min() > 0
+    assert np.allclose(Ad, Ad.T, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# Galerkin, colouring, Gauss-Seidel, Cholesky
+# ---------------------------------------------------------------------------
+def test_galerkin_brute_force_and_quadratic_form(torus_pin_hierarchy):
+    V, F = synth.perturbed_icosphere(1, seed=4)          # 42 vertices
+    A = oracle.system_matrix(V, F, 0.1)
+    rng = np.random.default_rng(1)
+    n, nc = 42, 12
+    P = np.zeros((n, nc))
+    for i in range(n):                                    # 3 barycentric weights per row
+        cols = rng.choice(nc, 3, replace=False)
+        w = rng.uniform(0.1, 1.0, 3)
+        P[i, cols] = w / w.sum()
+    Ac = oracle.galerkin(A, sp.csr_matrix(P)).toarray()
+    Ad = A.toarray()
+    brute = np.zeros((nc, nc))
+    for I in range(nc):
+        for J in range(nc):
+            s = 0.0
+            for i in range(n):
+                if P[i, I] == 0:
+                    continue
+                for j in range(n):
+                    s += P[i, I] * Ad[i, j] * P[j, J]
+            brute[I, J] = s
+    assert np.abs(Ac - brute).max() < 1e-14 * np.abs(brute).max()
+    x = rng.standard_normal(nc)
+    assert abs(x @ Ac @ x - (P @ x) @ Ad @ (P @ x)) < 1e-13 * abs(x @ Ac @ x)
+
+
+def test_colouring_matches_hand_worked_alg3():
+    txt = [l.split() for l in open(os.path.join(GOLDEN, "alg3_colouring_small.txt"))
+           if l.strip() and not l.startswith("#")]
+    d = {t[0]: [int(v) for v in t[1:]] for t in txt}
+    n = d["n"][0]
+    e = np.array(d["edges"]).reshape(-1, 2)
+    r = np.concatenate([e[:, 0], e[:, 1], np.arange(n)])
+    c = np.concatenate([e[:, 1], e[:, 0], np.arange(n)])
+    S = sp.csr_matrix((np.ones(r.size), (r, c)), shape=(n, n))
+    assert list(oracle.greedy_colouring(S)) == d["colours"]
+
+
+def test_colouring_is_proper_on_mesh_and_galerkin_patterns(torus_pin_hierarchy):
+    V, F, Ps = torus_pin_hierarchy
+    A = oracle.system_matrix(V, F, 1e-3)
+    for P in [None] + Ps:
+        if P is not None:
+            A = oracle.galerkin(A, P)
+        col = oracle.greedy_colouring(A)
+        coo = A.tocoo()
+        off = coo.row != coo.col
+        assert np.all(col[coo.row[off]] != col[coo.col[off]])
+
+
+def test_gauss_seidel_equals_matrix_splitting():
+    V, F = synth.perturbed_icosphere(2, seed=8)
+    A = oracle.system_matrix(V, F, 1e-2)
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal((A.shape[0], 2))
+    x0 = rng.standard_normal((A.shape[0], 2))
+    col = oracle.greedy_colouring(A)
+    for reverse in (False, True):
+        order = oracle.colour_order(col, reverse)
+        x = x0.copy()
+        oracle.gs_sweep(A, x, b, order)
+        Ap = A.toarray()[np.ix_(order, order)]
+        xp = sla.solve_triangular(np.tril(Ap), b[order] - np.triu(Ap, 1) @ x0[order], lower=True)
+        assert np.abs(x[order] - xp).max() < 1e-13 * np.abs(xp).max()
+        x32 = x0.astype(np.float32)
+        oracle.gs_sweep(A.astype(np.float32), x32, b.astype(np.float32), order)
+        assert np.abs(x32[order] - xp).max() < 1e-5 * np.abs(xp).max()
+
+
+def test_cholesky_against_lapack_and_not_spd():
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((30, 30))
+    A = B @ B.T + 30 * np.eye(30)
+    L = oracle.cholesky(A)
+    assert np.abs(L @ L.T - A).max() < 1e-13 * np.abs(A).max()
+    assert np.abs(L - np.linalg.cholesky(A)).max() < 1e-12 * np.abs(L).max()
+    b = rng.standard_normal((30, 3))
+    assert np.abs(oracle.chol_solve(L, b) - np.linalg.solve(A, b)).max() < 1e-12
+    A[5, 5] = -1.0
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.cholesky(A)
+
+
+# ---------------------------------------------------------------------------
+# cycle and solve
+# ---------------------------------------------------------------------------
+def test_single_level_cycle_is_direct_solve():
+    V, F = synth.perturbed_icosphere(2, seed=2)
+    A = oracle.system_matrix(V, F, 1e-2)
+    levels = oracle.build_levels(A, [])
+    b = synth.uniform_rhs(A.shape[0], seed=4)
+    x = oracle.vcycle(levels, 0, np.zeros_like(b), b, oracle.Options())
+    assert oracle.rel_residual(A, x, b) < 1e-13
+
+
+def test_identity_prolongation_cycle_is_exact():
+    V, F = synth.perturbed_icosphere(2, seed=2)
+    A = oracle.system_matrix(V, F, 1e-2)
+    levels = oracle.build_levels(A, [sp.identity(A.shape[0], format="csr")])
+    b = synth.uniform_rhs(A.shape[0], seed=4)
+    x = oracle.vcycle(levels, 0, np.zeros_like(b), b, oracle.Options())
+    assert oracle.rel_residual(A, x, b) < 1e-12
+
+
+def test_two_level_without_relaxation_is_coarse_correction(torus_pin_hierarchy):
+    V, F, Ps = torus_pin_hierarchy
+    A = oracle.system_matrix(V, F, 1e-3)
+    levels = oracle.build_levels(A, Ps[:1])
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(A.shape[0])
+    x0 = rng.standard_normal(A.shape[0])
+    opt = oracle.Options(mu_pre=0, mu_post=0)
+    x = oracle.vcycle(levels, 0, x0.copy(), b, opt)
+    P = Ps[0].toarray()
+    Ad = A.toarray()
+    expect = x0 + P @ np.linalg.solve(P.T @ Ad @ P, P.T @ (b - Ad @ x0))
+    assert np.abs(x - expect).max() < 1e-12 * np.abs(expect).max()
+
+
+def test_cycle_converges_to_direct_solution(torus_pin_hierarchy):
+    V, F, Ps = torus_pin_hierarchy
+    A = oracle.system_matrix(V, F, 1e-3)
+    levels = oracle.build_levels(A, Ps)
+    b = synth.uniform_rhs(A.shape[0], nrhs=2, seed=6)
+    res = oracle.solve(levels, b, opt=oracle.Options(rtol=1e-12))
+    xs = spla.splu(A.tocsc()).solve(b)
+    assert res.history[-1] <= 1e-12
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) < 1e-10
+    rho = oracle.convergence_factor(res.history)
+    assert 0 < rho < 0.5
+    assert all(h1 < h0 for h0, h1 in zip(res.history, res.history[1:]))
+
+
+def test_mixed_precision_reaches_direct_solution(torus_pin_hierarchy):
+    V, F, Ps = torus_pin_hierarchy
+    A = oracle.system_matrix(V, F, 1e-3)
+    levels = oracle.build_levels(A, Ps)
+    b = synth.uniform_rhs(A.shape[0], seed=9)
+    res = oracle.solve_mixed(levels, b, opt=oracle.Options(rtol=1e-10))
+    xs = spla.splu(A.tocsc()).solve(b)
+    assert res.history[-1] <= 1e-10
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) < 1e-9
+
+
+def test_dirichlet_reduction_solves_constrained_minimum():
+    V, F, bnd = synth.disk(16, seed=1)
+    n = V.shape[0]
+    A = oracle.system_matrix(V, F, 1e-2)
+    b = synth.uniform_rhs(n, seed=2)
+    Auu, _, u, _ = oracle.dirichlet_reduce(A, [], bnd)
+    xu = spla.spsolve(Auu.tocsc(), b[u])
+    x = np.zeros(n)
+    x[u] = xu
+    g = A @ x - b                       # gradient of 1/2 x'Ax - x'b
+    assert np.abs(g[u]).max() < 1e-12 * np.abs(b).max()
+
+
+def test_dirichlet_drops_empty_coarse_columns():
+    # fine 0..5, coarse 0..2; fine row 5 is known and is the only support of coarse 2
+    P1 = sp.csr_matrix(np.array([[1, 0, 0], [0, 1, 0], [.5, .5, 0], [.25, .75, 0],
+                                 [1, 0, 0], [0, 0, 1.]]))
+    P2 = sp.csr_matrix(np.array([[1.0, 0], [0, 1.0], [0.5, 0.5]]))
+    A = sp.identity(6, format="csr")
+    known = np.array([0, 0, 0, 0, 0, 1], dtype=bool)
+    Auu, Ps, u, keep = oracle.dirichlet_reduce(A, [P1, P2], known)
+    assert list(keep) == [0, 1]
+    assert Ps[0].shape == (5, 2) and Ps[1].shape == (2, 2)
+    assert np.allclose(Ps[1].toarray(), np.eye(2))
