@@ -1,0 +1,249 @@
+/*
+ * smg.h -- C ABI of the GB300 surface multigrid library (libsmg.so).
+ *
+ * Method: Liu, Zhang, Ben-Chen, Jacobson, "Surface Multigrid via Intrinsic
+ * Prolongation", ACM TOG 40(4), 2021.  Alg. 1 is the overall structure: the
+ * hierarchy P_1..P_H is precomputed from the mesh (V, F) alone; the system
+ * A x = b may change afterwards; V-cycles (Alg. 2) run until the error is
+ * below a tolerance.  Fig. "fourSteps" is the reason for the split between
+ * setup (geometry) and update (matrix) below.
+ *
+ * Conventions for every entry point
+ *   - Return value: SMG_OK (0) or one of the SMG_ERR_* codes; no exception or
+ *     longjmp ever crosses this boundary.  smg_last_error() gives a message
+ *     for the most recent failure on the calling thread.
+ *   - Host pointers are read during the call only and stay owned by the caller.
+ *   - Device pointers (suffix _dev) are owned by the caller, must hold the
+ *     documented number of elements, and are accessed in stream order on the
+ *     `stream` argument (a cudaStream_t passed as void*; NULL = legacy default).
+ *   - All floating-point arrays are IEEE binary64 unless stated otherwise.
+ *   - Vectors indexed by "unknowns" are in ascending original vertex order,
+ *     restricted to the vertices that are not Dirichlet-known.  Multi-RHS
+ *     arrays are row-major n x nrhs (the nrhs values of one vertex adjacent).
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef SMG_H
+#define SMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define SMG_OK                0
+#define SMG_ERR_INVALID_ARG   1  /* null pointer, size or index out of range      */
+#define SMG_ERR_NONMANIFOLD   2  /* mesh is not an oriented 2-manifold            */
+#define SMG_ERR_DECIMATION    3  /* hierarchy could not be built                  */
+#define SMG_ERR_NOT_SPD       4  /* a coarsest pivot was not positive             */
+#define SMG_ERR_NOT_CONVERGED 5  /* max_cycles reached above rtol (x still valid) */
+#define SMG_ERR_DIVERGED      6  /* residual became non-finite                    */
+#define SMG_ERR_TIMEOUT       7  /* a bounded device wait gave up                 */
+#define SMG_ERR_CUDA          8  /* a CUDA runtime call failed                    */
+#define SMG_ERR_NO_MEMORY     9  /* host or device allocation failed              */
+#define SMG_ERR_STATE        10  /* call out of order (e.g. solve before update)  */
+#define SMG_ERR_IO           11  /* plan file could not be read or written        */
+
+#define SMG_FP64  0   /* every cycle in binary64                                          */
+#define SMG_MIXED 1   /* binary32 V-cycles inside binary64 iterative refinement; the
+                         residual, the update and the coarsest Cholesky stay binary64 */
+
+typedef void *smg_stream;   /* a cudaStream_t */
+
+/*
+ * Options.  Defaults (smg_default_options) follow Sec. 5 and App. "Ablation":
+ * Gauss-Seidel with mu_pre = mu_post = 2, coarsening ratio 0.25, coarsest level
+ * no smaller than 500 vertices.
+ *   min_coarse   paper rule: stop when the next level would have fewer vertices
+ *   max_coarse   if > 0, replaces the rule above: coarsen while n > max_coarse
+ *   max_levels   if > 0, at most this many levels (finest included)
+ *   rtol         stop when max over right-hand sides of ||b - A x|| / ||b|| <= rtol
+ *   post_reverse 1: post-relaxation visits the colour classes in reverse order
+ *                (symmetric cycle); 0: same order as pre-relaxation
+ */
+typedef struct smg_options {
+    int32_t mu_pre;
+    int32_t mu_post;
+    double  ratio;
+    int64_t min_coarse;
+    int64_t max_coarse;
+    int32_t max_levels;
+    int32_t max_cycles;
+    double  rtol;
+    int32_t precision;     /* SMG_FP64 or SMG_MIXED */
+    int32_t post_reverse;
+} smg_options;
+
+/* Result of one solve (host struct filled by smg_solve). */
+typedef struct smg_info {
+    int32_t cycles;         /* V-cycles (or refinement steps) executed          */
+    int32_t status;         /* SMG_OK, SMG_ERR_NOT_CONVERGED or SMG_ERR_DIVERGED */
+    double  rel_residual0;  /* before the first cycle                           */
+    double  rel_residual;   /* after the last cycle                             */
+    double  rho;            /* (rel_residual / rel_residual0)^(1/cycles)        */
+} smg_info;
+
+void        smg_default_options(smg_options *opts);
+const char *smg_status_string(int status);
+const char *smg_last_error(void);
+
+/* =====================================================================
+ * Host-only setup ("plan"): decimation, self-parameterization, P, the
+ * symbolic coarse patterns, colourings.  Needs no GPU.
+ * ===================================================================== */
+typedef struct smg_plan smg_plan;
+
+/*
+ * Build the hierarchy from a triangle mesh (Alg. 1, "precompute multigrid
+ * hierarchy"; Sec. 4 and App. "SSP").
+ *   V  host n x 3 positions; F host m x 3 vertex indices, consistently oriented.
+ *   dirichlet_mask  host n bytes (nonzero = value known, zero Dirichlet data) or
+ *                   NULL; the system is reduced to the unknowns as in App.
+ *                   "Dirichlet Boundary Conditions" (the finest P keeps the rows
+ *                   of unknowns and drops all-zero columns together with the
+ *                   matching rows of the next P).
+ *   opts            NULL = defaults.
+ * The plan is owned by the library; free it with smg_plan_destroy.
+ */
+int  smg_plan_build(const double *V, int64_t n, const int32_t *F, int64_t m,
+                    const uint8_t *dirichlet_mask, const smg_options *opts, smg_plan **out);
+void smg_plan_destroy(smg_plan *plan);
+
+/* Number of levels H + 1 (level 0 = finest, level H = coarsest, solved directly). */
+int  smg_plan_num_levels(const smg_plan *plan);
+
+/* Level l operator: n rows, nnz structural entries (diagonal included) and the
+ * number of colour classes of Alg. 3 (0 at the coarsest level). */
+int  smg_plan_level_info(const smg_plan *plan, int level, int64_t *n, int64_t *nnz, int32_t *ncolours);
+
+/* Geometry of mesh level l (positions after decimation).  Pointers stay valid
+ * until the plan is destroyed. */
+int  smg_plan_mesh(const smg_plan *plan, int level, int64_t *n, int64_t *m,
+                   const double **V, const int32_t **F);
+
+/* P_l (level >= 1) as produced by the self-parameterization, before any
+ * Dirichlet reduction: n_{l-1} x 3 coarse vertex indices (-1 = unused slot) and
+ * weights, in the vertex numbering of mesh levels l-1 and l (Sec. 4.5: each row
+ * holds the barycentric coordinates of a fine vertex in a coarse triangle). */
+int  smg_plan_prolongation(const smg_plan *plan, int level, int64_t *n_fine, int64_t *n_coarse,
+                           const int32_t **idx, const double **w);
+
+/* Symbolic pattern of A_l (CSR, sorted columns, diagonal included) in the
+ * natural numbering of the reduced level (level 0: unknowns; level 1: kept
+ * coarse vertices), and its Alg. 3 colouring (level < H). */
+int  smg_plan_pattern(const smg_plan *plan, int level, const int64_t **rowptr, const int32_t **col);
+int  smg_plan_colouring(const smg_plan *plan, int level, const int32_t **colour);
+
+/* Level-0 unknowns (ascending original vertex ids) and the kept level-1
+ * vertices after the Dirichlet column drop. */
+int  smg_plan_unknowns(const smg_plan *plan, int64_t *nu, const int32_t **vertex_of_unknown);
+int  smg_plan_kept_coarse(const smg_plan *plan, int64_t *nk, const int32_t **kept);
+
+/* Decimation statistics of level l -> l+1: out[0..8] = collapses, rejected
+ * (link, boundary, flip, angle, quality, solve), clamped, and 1e15 x the most
+ * negative barycentric before clamping. */
+int  smg_plan_stats(const smg_plan *plan, int level, int64_t out[9]);
+
+/* Checkpoint / resume of the geometry-only setup (versioned binary file). */
+int  smg_plan_save(const smg_plan *plan, const char *path);
+int  smg_plan_load(const char *path, smg_plan **out);
+
+/* =====================================================================
+ * Device hierarchy: upload, per-frame update and solve (sm_103a kernels).
+ * ===================================================================== */
+typedef struct smg_hierarchy smg_hierarchy;
+
+/*
+ * Upload a plan to the current CUDA device (the plan may be destroyed after).
+ * Allocates every device workspace the solves need; later calls allocate only
+ * when a new right-hand-side count is first used.
+ */
+int  smg_create(const smg_plan *plan, const smg_options *opts, smg_hierarchy **out);
+/* smg_plan_build + smg_create. */
+int  smg_setup(const double *V, int64_t n, const int32_t *F, int64_t m,
+               const uint8_t *dirichlet_mask, const smg_options *opts, smg_hierarchy **out);
+void smg_destroy(smg_hierarchy *h);
+
+/* Replace rtol / max_cycles / precision / mu / post_reverse for later solves
+ * (decimation fields are ignored). */
+int  smg_set_options(smg_hierarchy *h, const smg_options *opts);
+
+/*
+ * Per-frame update (Alg. 1 "build left-hand-side" followed by the cached
+ * Galerkin hierarchy A_{h+1} = P_{h+1}^T A_h P_{h+1}, Eq. gca, and the
+ * Cholesky factor of A_H):
+ *   smg_update_positions  V_dev: n x 3 positions of ALL mesh vertices (same
+ *                         numbering as setup); assembles A = M + t L with the
+ *                         cotangent Laplacian L (positive semi-definite sign)
+ *                         and the barycentric lumped mass M.
+ *   smg_update_t          same with the last positions and a new t.
+ *   smg_update_matrix     vals_dev: user-supplied A on the level-0 pattern
+ *                         (smg_plan_pattern level 0, nnz values); must be
+ *                         symmetric positive definite.
+ * Asynchronous on `stream` except that smg_update_* returns SMG_ERR_NOT_SPD
+ * only from the next smg_solve (the pivot check is read there).
+ */
+int  smg_update_positions(smg_hierarchy *h, const double *V_dev, double t, smg_stream stream);
+int  smg_update_t(smg_hierarchy *h, double t, smg_stream stream);
+int  smg_update_matrix(smg_hierarchy *h, const double *vals_dev, smg_stream stream);
+
+/*
+ * Solve A x = b (Alg. 1 loop with Alg. 2 cycles), x_dev holding the initial
+ * guess on entry and the result on return.  b_dev, x_dev: nu x nrhs.
+ * One CUDA-graph launch runs every cycle and the device-side stopping test;
+ * the call then synchronises `stream` to fill `info` (may be NULL).
+ * Returns SMG_OK when converged, SMG_ERR_NOT_CONVERGED / SMG_ERR_DIVERGED
+ * otherwise (x_dev then holds the last iterate).  nrhs in 1..4.
+ */
+int  smg_solve(smg_hierarchy *h, const double *b_dev, double *x_dev, int nrhs, smg_info *info,
+               smg_stream stream);
+
+/* The same solve, only enqueued: nothing waits on the host.  After the caller
+ * has synchronised `stream`, smg_solve_result fills `info` and returns the
+ * status smg_solve would have returned.  Calls on one handle must not overlap. */
+int  smg_solve_async(smg_hierarchy *h, const double *b_dev, double *x_dev, int nrhs, smg_stream stream);
+int  smg_solve_result(smg_hierarchy *h, smg_info *info);
+
+/* Exactly one V-cycle of Alg. 2 from x_dev (precision SMG_FP64), asynchronous. */
+int  smg_vcycle(smg_hierarchy *h, const double *b_dev, double *x_dev, int nrhs, smg_stream stream);
+
+/* Lumped mass diagonal of the last smg_update_positions, unknowns order (nu),
+ * and y = M x for nu x nrhs arrays. */
+int  smg_mass(smg_hierarchy *h, double *m_dev, smg_stream stream);
+int  smg_apply_mass(smg_hierarchy *h, const double *x_dev, double *y_dev, int nrhs, smg_stream stream);
+
+/* Copy the values of A_l to the host, aligned with smg_plan_pattern(level)
+ * (natural numbering); synchronises `stream`. */
+int  smg_level_matrix(smg_hierarchy *h, int level, double *vals_host, smg_stream stream);
+
+/*
+ * Measurement hook: enqueue `count` repetitions of one stage on the
+ * hierarchy's internal level buffers (no host synchronisation, no gather or
+ * scatter), so a caller can time it with CUDA events on `stream`:
+ *   SMG_STAGE_CYCLE     one V-cycle (binary64) or one refinement step
+ *                       (SMG_MIXED: binary32 cycle + binary64 update), as a graph
+ *   SMG_STAGE_SWEEP     one forward multicolour Gauss-Seidel sweep at `level`
+ *   SMG_STAGE_RESIDUAL  r = b - A x at `level`
+ *   SMG_STAGE_GALERKIN  A_{level+1} = P^T A_level P
+ *   SMG_STAGE_FACTOR    the coarsest Cholesky factor and inverse factor
+ *   SMG_STAGE_UPDATE    the whole update graph (Galerkin chain + factor)
+ * Needs a previous update; the numerical content of the buffers is whatever
+ * the last solve left there.
+ */
+#define SMG_STAGE_CYCLE    0
+#define SMG_STAGE_SWEEP    1
+#define SMG_STAGE_RESIDUAL 2
+#define SMG_STAGE_GALERKIN 3
+#define SMG_STAGE_FACTOR   4
+#define SMG_STAGE_UPDATE   5
+int  smg_run_stage(smg_hierarchy *h, int stage, int level, int nrhs, int precision, int count,
+                   smg_stream stream);
+
+/* Device bytes held by the hierarchy. */
+int64_t smg_device_bytes(const smg_hierarchy *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMG_H */

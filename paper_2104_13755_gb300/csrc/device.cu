@@ -1,0 +1,658 @@
+// Device hierarchy: upload, update (assembly + Galerkin + coarsest factor),
+// graph-captured V-cycles and the device half of the C ABI.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "kernels.cuh"
+
+using namespace smg;
+
+namespace {
+
+struct CudaFail : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+
+inline void ck(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) throw CudaFail(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+inline unsigned blocks_for(int64_t work, int threads = kern::kThreads) {
+    return (unsigned)((work + threads - 1) / threads);
+}
+
+template <class T>
+T* dalloc(smg_hierarchy* h, int64_t count) {
+    if (count <= 0) count = 1;
+    void* p = nullptr;
+    ck(cudaMalloc(&p, sizeof(T) * (size_t)count), "cudaMalloc");
+    h->allocs.push_back(p);
+    h->bytes += (int64_t)(sizeof(T) * (size_t)count);
+    return (T*)p;
+}
+
+template <class T>
+T* upload(smg_hierarchy* h, const std::vector<T>& v) {
+    T* p = dalloc<T>(h, (int64_t)v.size());
+    if (!v.empty()) ck(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice), "upload");
+    return p;
+}
+
+std::vector<float> to_f32(const std::vector<double>& v) {
+    std::vector<float> o(v.size());
+    for (size_t k = 0; k < v.size(); k++) o[k] = (float)v[k];
+    return o;
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+struct LevelView {
+    const T *sval, *diag, *dinv, *p_w, *pt_w;
+    T *x, *b, *r;
+};
+
+template <typename T>
+LevelView<T> view(DLevel& L);
+template <>
+LevelView<double> view<double>(DLevel& L) {
+    return {L.vals + L.sbase, L.vals, L.dinv, L.p_w, L.pt_w, L.x, L.b, L.r};
+}
+template <>
+LevelView<float> view<float>(DLevel& L) {
+    return {L.vals32 + L.sbase, L.vals32, L.dinv32, L.p_w32, L.pt_w32, L.x32, L.b32, L.r32};
+}
+
+template <typename T, int K>
+void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse, cudaStream_t s) {
+    for (int cc = 0; cc < L.ncolours; cc++) {
+        const int c = reverse ? L.ncolours - 1 - cc : cc;
+        const int s0 = L.colour_slice[c], s1 = L.colour_slice[c + 1];
+        if (s1 <= s0) continue;
+        kern::gs_colour<T, K><<<blocks_for((int64_t)(s1 - s0) * 32), kern::kThreads, 0, s>>>(L.slices, s0, s1, L.sell_col,
+                                                                                            v.sval, v.dinv, b, x);
+    }
+}
+
+// One V-cycle of Alg. 2 on the level buffers (x_0, b_0 of the chosen precision).
+template <typename T, int K>
+void rec_vcycle(smg_hierarchy* h, bool zero_x0, cudaStream_t s) {
+    const int H = h->H;
+    const bool single = sizeof(T) == 4;
+    for (int l = 0; l < H; l++) {
+        DLevel& L = h->L[l];
+        DLevel& N = h->L[l + 1];
+        LevelView<T> v = view<T>(L);
+        LevelView<T> vn = view<T>(N);
+        if (l > 0 || zero_x0) ck(cudaMemsetAsync(v.x, 0, sizeof(T) * L.n * K, s), "memset");  // coarse levels start from 0
+        for (int it = 0; it < h->opts.mu_pre; it++) rec_sweep<T, K>(L, v, v.b, v.x, false, s);  // pre-relaxation
+        kern::residual<T, K><<<blocks_for((int64_t)L.nslices * 32), kern::kThreads, 0, s>>>(
+            L.slices, L.nslices, L.sell_col, v.sval, v.diag, v.b, v.x, v.r);
+        kern::restrict_rows<T, K><<<blocks_for(N.n), kern::kThreads, 0, s>>>((int)N.n, L.pt_ptr, L.pt_row, v.pt_w, v.r,
+                                                                             vn.b);
+    }
+    DLevel& C = h->L[H];
+    LevelView<T> vc = view<T>(C);
+    record_coarsest_solve(h, K, vc.b, single, vc.x, single, s);  // direct solve at level H
+    for (int l = H - 1; l >= 0; l--) {
+        DLevel& L = h->L[l];
+        DLevel& N = h->L[l + 1];
+        LevelView<T> v = view<T>(L);
+        LevelView<T> vn = view<T>(N);
+        kern::prolong_add<T, K><<<blocks_for(L.n), kern::kThreads, 0, s>>>((int)L.n, L.p_idx, v.p_w, vn.x, v.x);
+        for (int it = 0; it < h->opts.mu_post; it++) rec_sweep<T, K>(L, v, v.b, v.x, h->opts.post_reverse != 0, s);
+    }
+}
+
+// Level-0 residual norm partials (binary64), optionally writing the binary32 residual.
+template <int K>
+void rec_resnorm(smg_hierarchy* h, bool init, bool r32, cudaStream_t s) {
+    DLevel& L = h->L[0];
+    float* out32 = L.b32;
+    if (L.coarsest) {
+        const int n = (int)L.n;
+#define SMG_RN(I, R) kern::resnorm_dense<K, I, R><<<kern::kNormBlocks, kern::kThreads, 0, s>>>(n, L.vals, L.b, L.x, h->partials, out32)
+        if (init && r32) SMG_RN(true, true);
+        else if (init) SMG_RN(true, false);
+        else if (r32) SMG_RN(false, true);
+        else SMG_RN(false, false);
+#undef SMG_RN
+        return;
+    }
+#define SMG_RN(I, R)                                                                                         \
+    kern::resnorm<K, I, R><<<kern::kNormBlocks, kern::kThreads, 0, s>>>(L.slices, L.nslices, L.sell_col, \
+                                                                        L.vals + L.sbase, L.vals, L.b, L.x, \
+                                                                        h->partials, out32)
+    if (init && r32) SMG_RN(true, true);
+    else if (init) SMG_RN(true, false);
+    else if (r32) SMG_RN(false, true);
+    else SMG_RN(false, false);
+#undef SMG_RN
+}
+
+template <int K>
+void rec_cycle_fp64(smg_hierarchy* h, cudaStream_t s) {
+    if (h->H == 0) {
+        DLevel& C = h->L[0];
+        record_coarsest_solve(h, K, C.b, false, C.x, false, s);
+    } else {
+        rec_vcycle<double, K>(h, false, s);
+    }
+}
+
+template <int K>
+void rec_cycle_mixed(smg_hierarchy* h, cudaStream_t s) {
+    DLevel& L0 = h->L[0];
+    if (h->H == 0) record_coarsest_solve(h, K, L0.b32, true, L0.x32, true, s);
+    else rec_vcycle<float, K>(h, true, s);
+    kern::ir_update<<<blocks_for(L0.n * K), kern::kThreads, 0, s>>>(L0.n * K, L0.x32, L0.x);
+}
+
+template <int K>
+void rec_final(smg_hierarchy* h, cudaGraphConditionalHandle hnd, bool init, bool use_cond, cudaStream_t s) {
+    kern::norm_final<K><<<1, kern::kThreads, 0, s>>>(h->partials, kern::kNormBlocks, h->state, hnd, init ? 1 : 0,
+                                                     h->opts.rtol, h->opts.max_cycles, use_cond ? 1 : 0);
+}
+
+template <int K>
+cudaGraphExec_t build_solve_graph(smg_hierarchy* h, bool mixed) {
+    cudaStream_t s = h->cap;
+    cudaGraph_t g = nullptr;
+    ck(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    cudaGraphConditionalHandle hnd;
+    ck(cudaGraphConditionalHandleCreate(&hnd, g, 0, 0), "cudaGraphConditionalHandleCreate");
+    // before the loop: ||b||, the initial residual and the first stopping test
+    ck(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), "capture init");
+    rec_resnorm<K>(h, true, mixed, s);
+    rec_final<K>(h, hnd, true, true, s);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    ck(cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps), "capture info");
+    std::vector<cudaGraphNode_t> frontier(deps, deps + ndeps);
+    ck(cudaGetLastError(), "init launches");
+    ck(cudaStreamEndCapture(s, &g), "end capture init");
+    // WHILE node: one cycle, the residual norm and the stopping test per iteration
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    ck(cudaGraphAddNode(&wnode, g, frontier.data(), nullptr, frontier.size(), &cp), "add while node");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ck(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), "capture body");
+    if (mixed) rec_cycle_mixed<K>(h, s);
+    else rec_cycle_fp64<K>(h, s);
+    rec_resnorm<K>(h, false, mixed, s);
+    rec_final<K>(h, hnd, false, true, s);
+    ck(cudaGetLastError(), "body launches");
+    ck(cudaStreamEndCapture(s, &body), "end capture body");
+    cudaGraphExec_t exec = nullptr;
+    ck(cudaGraphInstantiate(&exec, g, 0), "instantiate solve graph");
+    cudaGraphDestroy(g);
+    return exec;
+}
+
+template <int K>
+cudaGraphExec_t build_cycle_graph(smg_hierarchy* h, bool mixed) {
+    cudaStream_t s = h->cap;
+    cudaGraph_t g = nullptr;
+    ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture cycle");
+    if (mixed) rec_cycle_mixed<K>(h, s);
+    else rec_cycle_fp64<K>(h, s);
+    ck(cudaGetLastError(), "cycle launches");
+    ck(cudaStreamEndCapture(s, &g), "end capture cycle");
+    cudaGraphExec_t exec = nullptr;
+    ck(cudaGraphInstantiate(&exec, g, 0), "instantiate cycle graph");
+    cudaGraphDestroy(g);
+    return exec;
+}
+
+cudaGraphExec_t solve_graph(smg_hierarchy* h, int K, bool mixed) {
+    const int key = (mixed ? 16 : 0) + K;
+    auto it = h->solve_exec.find(key);
+    if (it != h->solve_exec.end()) return it->second;
+    cudaGraphExec_t e = nullptr;
+    switch (K) {
+        case 1: e = build_solve_graph<1>(h, mixed); break;
+        case 2: e = build_solve_graph<2>(h, mixed); break;
+        case 3: e = build_solve_graph<3>(h, mixed); break;
+        default: e = build_solve_graph<4>(h, mixed); break;
+    }
+    h->solve_exec[key] = e;
+    return e;
+}
+
+cudaGraphExec_t cycle_graph(smg_hierarchy* h, int K, bool mixed) {
+    const int key = (mixed ? 16 : 0) + K;
+    auto it = h->cycle_exec.find(key);
+    if (it != h->cycle_exec.end()) return it->second;
+    cudaGraphExec_t e = nullptr;
+    switch (K) {
+        case 1: e = build_cycle_graph<1>(h, mixed); break;
+        case 2: e = build_cycle_graph<2>(h, mixed); break;
+        case 3: e = build_cycle_graph<3>(h, mixed); break;
+        default: e = build_cycle_graph<4>(h, mixed); break;
+    }
+    h->cycle_exec[key] = e;
+    return e;
+}
+
+// Galerkin chain, level preparation and the coarsest factor, as one graph.
+void build_update_graph(smg_hierarchy* h) {
+    cudaStream_t s = h->cap;
+    cudaGraph_t g = nullptr;
+    ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture update");
+    ck(cudaMemsetAsync(&h->state->chol_bad, 0, sizeof(int32_t), s), "memset");
+    for (int l = 0; l < h->H; l++) {
+        DLevel& L = h->L[l];
+        DLevel& N = h->L[l + 1];
+        kern::galerkin<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_w, L.vals, N.vals);
+    }
+    for (int l = 0; l < h->H; l++) {
+        DLevel& L = h->L[l];
+        kern::prep_level<<<blocks_for(L.nflat), kern::kThreads, 0, s>>>(L.nflat, L.n, L.vals, L.dinv, L.vals32,
+                                                                      L.dinv32);
+    }
+    record_coarsest_factor(h, s);
+    ck(cudaGetLastError(), "update launches");
+    ck(cudaStreamEndCapture(s, &g), "end capture update");
+    ck(cudaGraphInstantiate(&h->update_exec, g, 0), "instantiate update graph");
+    cudaGraphDestroy(g);
+}
+
+void drop_graphs(smg_hierarchy* h) {
+    for (auto& kv : h->solve_exec) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : h->cycle_exec) cudaGraphExecDestroy(kv.second);
+    h->solve_exec.clear();
+    h->cycle_exec.clear();
+}
+
+void free_all(smg_hierarchy* h) {
+    drop_graphs(h);
+    if (h->update_exec) cudaGraphExecDestroy(h->update_exec);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->state_host) cudaFreeHost(h->state_host);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    h->allocs.clear();
+}
+
+void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
+    ck(cudaGetDevice(&h->device), "cudaGetDevice");
+    h->opts = o;
+    h->H = (int)P.L.size() - 1;
+    ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    h->L.resize(P.L.size());
+    for (int l = 0; l <= h->H; l++) {
+        const LevelPlan& lp = P.L[l];
+        DLevel& L = h->L[l];
+        L.n = lp.n;
+        L.coarsest = lp.coarsest;
+        L.sbase = lp.sbase;
+        L.nflat = lp.nflat;
+        L.nslots = lp.nslots;
+        L.ncolours = lp.ncolours;
+        L.nslices = (int)lp.slices.size();
+        L.colour_slice = lp.colour_slice;
+        L.flat_to_csr = lp.flat_to_csr;
+        L.nnz_csr = (int64_t)lp.col.size();
+        L.vals = dalloc<double>(h, L.nflat);
+        ck(cudaMemset(L.vals, 0, sizeof(double) * L.nflat), "memset");
+        L.x = dalloc<double>(h, L.n * kMaxRhs);
+        L.b = dalloc<double>(h, L.n * kMaxRhs);
+        L.r = dalloc<double>(h, L.n * kMaxRhs);
+        L.x32 = dalloc<float>(h, L.n * kMaxRhs);
+        L.b32 = dalloc<float>(h, L.n * kMaxRhs);
+        L.r32 = dalloc<float>(h, L.n * kMaxRhs);
+        if (L.coarsest) {
+            L.np = (L.n + kDenseNB - 1) / kDenseNB * kDenseNB;
+            L.chol = dalloc<double>(h, L.np * L.np);
+            L.linv = dalloc<double>(h, L.np * L.np);
+            L.linvT = dalloc<double>(h, L.np * L.np);
+            L.dblk = dalloc<double>(h, L.np * kDenseNB);
+            L.y = dalloc<double>(h, L.n * kMaxRhs);
+            continue;
+        }
+        L.slices = upload(h, lp.slices);
+        L.sell_col = upload(h, lp.sell_col);
+        L.dinv = dalloc<double>(h, L.n);
+        L.vals32 = dalloc<float>(h, L.nflat);
+        L.dinv32 = dalloc<float>(h, L.n);
+        L.p_idx = upload(h, lp.p_idx);
+        L.p_w = upload(h, lp.p_w);
+        L.p_w32 = upload(h, to_f32(lp.p_w));
+        L.pt_ptr = upload(h, lp.pt_ptr);
+        L.pt_row = upload(h, lp.pt_row);
+        L.pt_w = upload(h, lp.pt_w);
+        L.pt_w32 = upload(h, to_f32(lp.pt_w));
+        L.g_ptr = upload(h, lp.g_ptr);
+        L.g_src = upload(h, lp.g_src);
+        L.g_w = upload(h, lp.g_w);
+        L.g_nnz = (int64_t)lp.g_src.size();
+    }
+    const AssemblyPlan& A = P.asmb;
+    h->nv = A.nv;
+    h->nf = A.nf;
+    h->nu = P.L[0].n;
+    h->F = upload(h, A.F);
+    h->facegeom = dalloc<double>(h, 4 * A.nf);
+    h->inc_ptr = upload(h, A.inc_ptr);
+    h->inc_code = upload(h, A.inc_code);
+    h->opp0 = upload(h, A.opp0);
+    h->opp1 = upload(h, A.opp1);
+    h->flat_to_user = upload(h, A.flat_to_user);
+    h->nnz_user = (int64_t)P.L[0].col.size();
+    h->Lflat0 = dalloc<double>(h, P.L[0].nflat);
+    ck(cudaMemset(h->Lflat0, 0, sizeof(double) * P.L[0].nflat), "memset");
+    h->Mdiag = dalloc<double>(h, P.L[0].n);
+    h->perm0 = upload(h, P.L[0].perm);
+    h->state = dalloc<SolveState>(h, 1);
+    ck(cudaMemset(h->state, 0, sizeof(SolveState)), "memset");
+    h->partials = dalloc<double>(h, (int64_t)kern::kNormBlocks * 2 * kMaxRhs);
+    ck(cudaMallocHost((void**)&h->state_host, sizeof(SolveState)), "cudaMallocHost");
+    build_update_graph(h);
+    ck(cudaDeviceSynchronize(), "setup");
+}
+
+int fail(const std::string& msg, int code) {
+    set_error(msg);
+    return code;
+}
+
+#define SMG_GUARD_BEGIN try {
+#define SMG_GUARD_END                                      \
+    }                                                      \
+    catch (const CudaFail& e) {                            \
+        return fail(e.what(), SMG_ERR_CUDA);               \
+    }                                                      \
+    catch (const std::bad_alloc&) {                        \
+        return fail("host allocation failed", SMG_ERR_NO_MEMORY); \
+    }
+
+}  // namespace
+
+extern "C" {
+
+int smg_create(const smg_plan* plan, const smg_options* opts, smg_hierarchy** out) {
+    if (!plan || !out) return fail("null plan or out", SMG_ERR_INVALID_ARG);
+    *out = nullptr;
+    smg_options o = plan->p.opts;
+    if (opts) {  // solve-time fields from opts; decimation fields stay those of the plan
+        o.mu_pre = opts->mu_pre;
+        o.mu_post = opts->mu_post;
+        o.max_cycles = opts->max_cycles;
+        o.rtol = opts->rtol;
+        o.precision = opts->precision;
+        o.post_reverse = opts->post_reverse;
+    }
+    if (o.mu_pre < 0 || o.mu_post < 0 || o.max_cycles < 0 || !(o.rtol >= 0))
+        return fail("invalid solve options", SMG_ERR_INVALID_ARG);
+    smg_hierarchy* h = new (std::nothrow) smg_hierarchy();
+    if (!h) return SMG_ERR_NO_MEMORY;
+    try {
+        create_impl(plan->p, o, h);
+    } catch (const CudaFail& e) {
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return fail(e.what(), std::string(e.what()).find("out of memory") != std::string::npos ? SMG_ERR_NO_MEMORY
+                                                                                                 : SMG_ERR_CUDA);
+    } catch (const std::bad_alloc&) {
+        free_all(h);
+        delete h;
+        return fail("host allocation failed", SMG_ERR_NO_MEMORY);
+    }
+    *out = h;
+    return SMG_OK;
+}
+
+int smg_setup(const double* V, int64_t n, const int32_t* F, int64_t m, const uint8_t* mask, const smg_options* opts,
+              smg_hierarchy** out) {
+    smg_plan* p = nullptr;
+    int st = smg_plan_build(V, n, F, m, mask, opts, &p);
+    if (st != SMG_OK) return st;
+    st = smg_create(p, opts, out);
+    smg_plan_destroy(p);
+    return st;
+}
+
+void smg_destroy(smg_hierarchy* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->cap);
+    free_all(h);
+    delete h;
+}
+
+int smg_set_options(smg_hierarchy* h, const smg_options* o) {
+    if (!h || !o) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (o->mu_pre < 0 || o->mu_post < 0 || o->max_cycles < 0 || !(o->rtol >= 0) ||
+        (o->precision != SMG_FP64 && o->precision != SMG_MIXED))
+        return fail("invalid solve options", SMG_ERR_INVALID_ARG);
+    h->opts.mu_pre = o->mu_pre;
+    h->opts.mu_post = o->mu_post;
+    h->opts.max_cycles = o->max_cycles;
+    h->opts.rtol = o->rtol;
+    h->opts.precision = o->precision;
+    h->opts.post_reverse = o->post_reverse;
+    drop_graphs(h);
+    return SMG_OK;
+}
+
+int smg_update_positions(smg_hierarchy* h, const double* V, double t, smg_stream stream) {
+    if (!h || !V) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (!std::isfinite(t)) return fail("t must be finite", SMG_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    DLevel& L0 = h->L[0];
+    const int64_t dense_n = L0.coarsest ? L0.n : 0;
+    kern::face_geom<<<blocks_for(h->nf), kern::kThreads, 0, s>>>(h->nf, h->F, V, h->facegeom);
+    kern::asm_diag<<<blocks_for(L0.n), kern::kThreads, 0, s>>>(L0.n, L0.coarsest ? L0.n + 1 : 1, h->inc_ptr,
+                                                               h->inc_code, h->facegeom, h->Lflat0, h->Mdiag);
+    const int64_t first = L0.coarsest ? 0 : L0.sbase;
+    kern::asm_off<<<blocks_for(L0.nflat - first), kern::kThreads, 0, s>>>(L0.nflat, first, dense_n, h->opp0, h->opp1,
+                                                                          h->facegeom, h->Lflat0);
+    kern::combine<<<blocks_for(L0.nflat), kern::kThreads, 0, s>>>(L0.nflat, L0.n, dense_n, t, h->Lflat0, h->Mdiag,
+                                                                  L0.vals);
+    ck(cudaGetLastError(), "assembly launches");
+    ck(cudaGraphLaunch(h->update_exec, s), "update graph");
+    h->have_positions = h->have_matrix = true;
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_update_t(smg_hierarchy* h, double t, smg_stream stream) {
+    if (!h) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (!h->have_positions) return fail("smg_update_t needs a previous smg_update_positions", SMG_ERR_STATE);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    DLevel& L0 = h->L[0];
+    kern::combine<<<blocks_for(L0.nflat), kern::kThreads, 0, s>>>(L0.nflat, L0.n, L0.coarsest ? L0.n : 0, t, h->Lflat0,
+                                                                  h->Mdiag, L0.vals);
+    ck(cudaGetLastError(), "combine launch");
+    ck(cudaGraphLaunch(h->update_exec, s), "update graph");
+    h->have_matrix = true;
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_update_matrix(smg_hierarchy* h, const double* vals, smg_stream stream) {
+    if (!h || !vals) return fail("null argument", SMG_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    DLevel& L0 = h->L[0];
+    kern::scatter_user<<<blocks_for(L0.nflat), kern::kThreads, 0, s>>>(L0.nflat, h->flat_to_user, vals, L0.vals);
+    ck(cudaGetLastError(), "scatter launch");
+    ck(cudaGraphLaunch(h->update_exec, s), "update graph");
+    h->have_matrix = true;
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+static int check_solve_args(smg_hierarchy* h, const double* b, double* x, int nrhs) {
+    if (!h || !b || !x) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (nrhs < 1 || nrhs > kMaxRhs) return fail("nrhs must be 1..4", SMG_ERR_INVALID_ARG);
+    if (!h->have_matrix) return fail("solve before any update", SMG_ERR_STATE);
+    return SMG_OK;
+}
+
+int smg_solve_async(smg_hierarchy* h, const double* b, double* x, int nrhs, smg_stream stream) {
+    int st = check_solve_args(h, b, x, nrhs);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    DLevel& L0 = h->L[0];
+    const int64_t m = L0.n * nrhs;
+    const bool mixed = h->opts.precision == SMG_MIXED;
+    cudaGraphExec_t e = solve_graph(h, nrhs, mixed);
+    kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, b, L0.b);
+    kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, x, L0.x);
+    ck(cudaGetLastError(), "gather");
+    ck(cudaGraphLaunch(e, s), "solve graph");
+    kern::scatter_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, L0.x, x);
+    ck(cudaGetLastError(), "scatter");
+    ck(cudaMemcpyAsync(h->state_host, h->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s), "state copy");
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_solve_result(smg_hierarchy* h, smg_info* info) {
+    if (!h) return fail("null argument", SMG_ERR_INVALID_ARG);
+    const SolveState& ss = *h->state_host;
+    if (info) {
+        info->cycles = ss.cycles;
+        info->status = ss.status;
+        info->rel_residual0 = ss.rel0;
+        info->rel_residual = ss.rel;
+        info->rho = (ss.cycles > 0 && ss.rel0 > 0) ? std::pow(ss.rel / ss.rel0, 1.0 / ss.cycles) : 0.0;
+    }
+    if (ss.chol_bad) return fail("coarsest operator is not positive definite", SMG_ERR_NOT_SPD);
+    if (ss.status == SMG_ERR_NOT_CONVERGED) return fail("not converged within max_cycles", ss.status);
+    if (ss.status == SMG_ERR_DIVERGED) return fail("residual became non-finite", ss.status);
+    return SMG_OK;
+}
+
+int smg_solve(smg_hierarchy* h, const double* b, double* x, int nrhs, smg_info* info, smg_stream stream) {
+    int st = smg_solve_async(h, b, x, nrhs, stream);
+    if (st) return st;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(std::string("solve: ") + cudaGetErrorString(e), SMG_ERR_CUDA);
+    return smg_solve_result(h, info);
+}
+
+int smg_vcycle(smg_hierarchy* h, const double* b, double* x, int nrhs, smg_stream stream) {
+    int st = check_solve_args(h, b, x, nrhs);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    DLevel& L0 = h->L[0];
+    const int64_t m = L0.n * nrhs;
+    cudaGraphExec_t e = cycle_graph(h, nrhs, false);
+    kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, b, L0.b);
+    kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, x, L0.x);
+    ck(cudaGetLastError(), "gather");
+    ck(cudaGraphLaunch(e, s), "vcycle graph");
+    kern::scatter_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, L0.x, x);
+    ck(cudaGetLastError(), "scatter");
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_mass(smg_hierarchy* h, double* m_dev, smg_stream stream) {
+    if (!h || !m_dev) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (!h->have_positions) return fail("smg_mass needs smg_update_positions", SMG_ERR_STATE);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    kern::scatter_rows<double><<<blocks_for(h->nu), kern::kThreads, 0, s>>>(h->nu, 1, h->perm0, h->Mdiag, m_dev);
+    ck(cudaGetLastError(), "mass");
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_apply_mass(smg_hierarchy* h, const double* x, double* y, int nrhs, smg_stream stream) {
+    if (!h || !x || !y || nrhs < 1) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    if (!h->have_positions) return fail("smg_apply_mass needs smg_update_positions", SMG_ERR_STATE);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    kern::apply_mass<<<blocks_for(h->nu * nrhs), kern::kThreads, 0, s>>>(h->nu, nrhs, h->perm0, h->Mdiag, x, y);
+    ck(cudaGetLastError(), "apply mass");
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_level_matrix(smg_hierarchy* h, int level, double* out, smg_stream stream) {
+    if (!h || !out || level < 0 || level > h->H) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    DLevel& L = h->L[level];
+    std::vector<double> flat(L.nflat);
+    ck(cudaMemcpyAsync(flat.data(), L.vals, sizeof(double) * L.nflat, cudaMemcpyDeviceToHost, s), "copy");
+    ck(cudaStreamSynchronize(s), "sync");
+    for (int64_t k = 0; k < L.nnz_csr; k++) out[k] = 0.0;
+    for (int64_t e = 0; e < L.nflat; e++)
+        if (L.flat_to_csr[e] >= 0) out[L.flat_to_csr[e]] = flat[e];
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_run_stage(smg_hierarchy* h, int stage, int level, int nrhs, int precision, int count, smg_stream stream) {
+    if (!h || nrhs < 1 || nrhs > kMaxRhs || count < 0 || level < 0 || level > h->H)
+        return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    if (!h->have_matrix) return fail("stage before any update", SMG_ERR_STATE);
+    const bool mixed = precision == SMG_MIXED;
+    const bool needs_fine = stage == SMG_STAGE_SWEEP || stage == SMG_STAGE_RESIDUAL || stage == SMG_STAGE_GALERKIN;
+    if (needs_fine && level >= h->H) return fail("level has no sparse operator", SMG_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    DLevel& L = h->L[level];
+    cudaGraphExec_t e = nullptr;
+    if (stage == SMG_STAGE_CYCLE) e = cycle_graph(h, nrhs, mixed);
+    for (int it = 0; it < count; it++) {
+        switch (stage) {
+            case SMG_STAGE_CYCLE: ck(cudaGraphLaunch(e, s), "cycle graph"); break;
+            case SMG_STAGE_SWEEP:
+                if (mixed) {
+                    LevelView<float> v = view<float>(L);
+                    switch (nrhs) {
+                        case 1: rec_sweep<float, 1>(L, v, v.b, v.x, false, s); break;
+                        case 2: rec_sweep<float, 2>(L, v, v.b, v.x, false, s); break;
+                        case 3: rec_sweep<float, 3>(L, v, v.b, v.x, false, s); break;
+                        default: rec_sweep<float, 4>(L, v, v.b, v.x, false, s); break;
+                    }
+                } else {
+                    LevelView<double> v = view<double>(L);
+                    switch (nrhs) {
+                        case 1: rec_sweep<double, 1>(L, v, v.b, v.x, false, s); break;
+                        case 2: rec_sweep<double, 2>(L, v, v.b, v.x, false, s); break;
+                        case 3: rec_sweep<double, 3>(L, v, v.b, v.x, false, s); break;
+                        default: rec_sweep<double, 4>(L, v, v.b, v.x, false, s); break;
+                    }
+                }
+                break;
+            case SMG_STAGE_RESIDUAL: {
+                LevelView<double> v = view<double>(L);
+                kern::residual<double, 1><<<blocks_for((int64_t)L.nslices * 32), kern::kThreads, 0, s>>>(
+                    L.slices, L.nslices, L.sell_col, v.sval, v.diag, v.b, v.x, v.r);
+                break;
+            }
+            case SMG_STAGE_GALERKIN: {
+                DLevel& N = h->L[level + 1];
+                kern::galerkin<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_w,
+                                                                            L.vals, N.vals);
+                break;
+            }
+            case SMG_STAGE_FACTOR: record_coarsest_factor(h, s); break;
+            case SMG_STAGE_UPDATE: ck(cudaGraphLaunch(h->update_exec, s), "update graph"); break;
+            default: return fail("unknown stage", SMG_ERR_INVALID_ARG);
+        }
+    }
+    ck(cudaGetLastError(), "stage launches");
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int64_t smg_device_bytes(const smg_hierarchy* h) { return h ? h->bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal: device-resident hierarchy shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace smg {
+
+constexpr int kMaxRhs = 4;
+constexpr int kDenseNB = 32;  // block size of the coarsest dense factorisation
+
+// Device-side solve bookkeeping (one per hierarchy).
+struct SolveState {
+    double bnorm2[kMaxRhs];  // ||b_r||^2 of the current right-hand sides
+    double rel0;             // relative residual before the first cycle
+    double rel;              // after the last cycle
+    int32_t cycles;
+    int32_t status;          // SMG_OK / SMG_ERR_NOT_CONVERGED / SMG_ERR_DIVERGED / -1 running
+    int32_t chol_bad;        // nonzero: a coarsest pivot was not positive
+    int32_t pad;
+};
+
+struct DLevel {
+    int64_t n = 0, sbase = 0, nflat = 0, nslots = 0;
+    bool coarsest = false;
+    int ncolours = 0, nslices = 0;
+    std::vector<int32_t> colour_slice;  // host copy, ncolours + 1
+    SliceMeta* slices = nullptr;
+    int32_t* sell_col = nullptr;
+    double* vals = nullptr;  // flat A_l
+    double* dinv = nullptr;
+    float* vals32 = nullptr;
+    float* dinv32 = nullptr;
+    // transfer to level l + 1
+    int32_t* p_idx = nullptr;  // [3][n]
+    double* p_w = nullptr;
+    float* p_w32 = nullptr;
+    int32_t* pt_ptr = nullptr;
+    int32_t* pt_row = nullptr;
+    double* pt_w = nullptr;
+    float* pt_w32 = nullptr;
+    int64_t* g_ptr = nullptr;
+    int32_t* g_src = nullptr;
+    double* g_w = nullptr;
+    int64_t g_nnz = 0;
+    // vectors, capacity n * kMaxRhs
+    double *x = nullptr, *b = nullptr, *r = nullptr;
+    float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+    // coarsest: padded dense factor, its inverse and the inverse transposed
+    int64_t np = 0;
+    double *chol = nullptr, *linv = nullptr, *linvT = nullptr, *dblk = nullptr, *y = nullptr;
+    // read-back map
+    std::vector<int64_t> flat_to_csr;
+    int64_t nnz_csr = 0;
+};
+
+}  // namespace smg
+
+struct smg_hierarchy {
+    smg_options opts{};
+    int H = 0;
+    std::vector<smg::DLevel> L;
+    // level-0 assembly
+    int64_t nv = 0, nf = 0, nu = 0;
+    int32_t* F = nullptr;
+    double* facegeom = nullptr;  // 4 per face: cot at corners 0..2, area
+    int32_t* inc_ptr = nullptr;
+    int32_t* inc_code = nullptr;
+    int32_t* opp0 = nullptr;
+    int32_t* opp1 = nullptr;
+    int64_t* flat_to_user = nullptr;
+    int64_t nnz_user = 0;
+    double* Lflat0 = nullptr;  // t-independent cotan values on the level-0 flat layout
+    double* Mdiag = nullptr;   // lumped mass, permuted level-0 rows
+    int32_t* perm0 = nullptr;  // permuted level-0 row -> unknown index
+    bool have_positions = false, have_matrix = false;
+    // solve state
+    smg::SolveState* state = nullptr;
+    smg::SolveState* state_host = nullptr;  // pinned
+    double* partials = nullptr;             // [kNormBlocks][2 * kMaxRhs]
+    cudaStream_t cap = nullptr;             // private capture stream
+    cudaGraphExec_t update_exec = nullptr;
+    std::map<int, cudaGraphExec_t> solve_exec;   // key precision * 16 + nrhs
+    std::map<int, cudaGraphExec_t> cycle_exec;   // key precision * 16 + nrhs
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    int device = 0;
+};
+
+namespace smg {
+// dense.cu: record the coarsest factorisation (Cholesky, then the inverse factor
+// and its transpose) on `s`; launches only, capturable.
+void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s);
+// dense.cu: x = A_H^{-1} b through the inverse factor; `in`/`out` are binary64 or
+// binary32 vectors (n x K row-major) as the flags say.
+void record_coarsest_solve(smg_hierarchy* h, int K, const void* in, bool in32, void* out, bool out32,
+                           cudaStream_t s);
+}  // namespace smg

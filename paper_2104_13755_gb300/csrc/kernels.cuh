@@ -1,0 +1,442 @@
+// Sparse kernels of the V-cycle (Alg. 2) and the per-frame update.
+//
+// Layout (per level, rows permuted colour-major): the off-diagonal entries sit in
+// SELL-32 slices -- 32 consecutive rows of one colour class, entry k of lane r at
+// slot off + 32 k + r -- so every warp-wide load of values or column indices is
+// one contiguous, aligned 128/256-byte segment.  The diagonal is stored apart
+// (and its reciprocal for the Gauss-Seidel update).  Vectors with K right-hand
+// sides are row-major n x K, so a neighbour gather reads K adjacent values.
+#pragma once
+
+#include "device.hpp"
+
+namespace smg {
+namespace kern {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kNormBlocks = 608;  // fixed grid of the deterministic norm reduction
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) {
+    return __ldg(p);
+}
+
+// ---------------------------------------------------------------------------
+// Multicolour Gauss-Seidel (App. "Multi-Color Gauss Seidel"): one colour class,
+// x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii for every row i of the class.
+// No row of a class is coupled to another row of the same class, so the rows
+// update in parallel and the x values read here are not written by this launch.
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) gs_colour(const SliceMeta* __restrict__ slices, int s0, int s1,
+                                                      const int32_t* __restrict__ col, const T* __restrict__ sval,
+                                                      const T* __restrict__ dinv, const T* __restrict__ b,
+                                                      T* __restrict__ x) {
+    const int s = s0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= s1) return;
+    const SliceMeta m = slices[s];
+    const int row = m.row0 + lane;
+    const bool valid = lane < m.nrows;
+    T acc[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) acc[q] = valid ? b[(int64_t)row * K + q] : T(0);
+    const int32_t* cp = col + m.off + lane;
+    const T* vp = sval + m.off + lane;
+#pragma unroll 4
+    for (int k = 0; k < m.width; k++) {
+        const int c = ldg(cp + k * 32);
+        const T v = ldg(vp + k * 32);
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] -= v * ldg(x + (int64_t)c * K + q);
+    }
+    if (valid) {
+        const T d = dinv[row];
+#pragma unroll
+        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = acc[q] * d;
+    }
+}
+
+// r = b - A x over all rows of a level.
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) residual(const SliceMeta* __restrict__ slices, int nslices,
+                                                     const int32_t* __restrict__ col, const T* __restrict__ sval,
+                                                     const T* __restrict__ diag, const T* __restrict__ b,
+                                                     const T* __restrict__ x, T* __restrict__ r) {
+    const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    const SliceMeta m = slices[s];
+    const int row = m.row0 + lane;
+    if (lane >= m.nrows) return;
+    T acc[K];
+    const T d = diag[row];
+#pragma unroll
+    for (int q = 0; q < K; q++) acc[q] = b[(int64_t)row * K + q] - d * x[(int64_t)row * K + q];
+    const int32_t* cp = col + m.off + lane;
+    const T* vp = sval + m.off + lane;
+#pragma unroll 4
+    for (int k = 0; k < m.width; k++) {
+        const int c = ldg(cp + k * 32);
+        const T v = ldg(vp + k * 32);
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] -= v * ldg(x + (int64_t)c * K + q);
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) r[(int64_t)row * K + q] = acc[q];
+}
+
+// Restriction r_{h+1} = P^T r_h (Alg. 2 "restrict residual"), one coarse row per
+// thread through the CSR of P^T: a deterministic gather.
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) restrict_rows(int nc, const int32_t* __restrict__ ptr,
+                                                          const int32_t* __restrict__ rows, const T* __restrict__ w,
+                                                          const T* __restrict__ r, T* __restrict__ bc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    T acc[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) acc[q] = T(0);
+    for (int k = ptr[I]; k < ptr[I + 1]; k++) {
+        const int i = rows[k];
+        const T wk = w[k];
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] += wk * ldg(r + (int64_t)i * K + q);
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) bc[(int64_t)I * K + q] = acc[q];
+}
+
+// Prolongation with the correction add, x_h <- x_h + P c (Alg. 2 "prolong
+// correction", "update solution"): three barycentric weights per fine row.
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) prolong_add(int n, const int32_t* __restrict__ idx,
+                                                        const T* __restrict__ w, const T* __restrict__ xc,
+                                                        T* __restrict__ x) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    T acc[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) acc[q] = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int c = idx[(int64_t)a * n + p];
+        const T wa = w[(int64_t)a * n + p];
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] += wa * ldg(xc + (int64_t)c * K + q);
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) x[(int64_t)p * K + q] += acc[q];
+}
+
+// ---------------------------------------------------------------------------
+// Level-0 residual norms for the stopping test of Alg. 1, reduced in a fixed
+// order (fixed grid, fixed tree) so the result is bitwise reproducible.
+// INIT also accumulates ||b||^2; R32 also stores the residual in binary32 (the
+// right-hand side of the next inner cycle of the mixed-precision form).
+template <int K, bool INIT, bool R32>
+__global__ void __launch_bounds__(kThreads) resnorm(const SliceMeta* __restrict__ slices, int nslices,
+                                                    const int32_t* __restrict__ col, const double* __restrict__ sval,
+                                                    const double* __restrict__ diag, const double* __restrict__ b,
+                                                    const double* __restrict__ x, double* __restrict__ partials,
+                                                    float* __restrict__ r32) {
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    double rr[K], bb[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) rr[q] = bb[q] = 0.0;
+    for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < nslices; s += gridDim.x * kWarps) {
+        const SliceMeta m = slices[s];
+        const int row = m.row0 + lane;
+        if (lane >= m.nrows) continue;
+        double acc[K];
+        const double d = diag[row];
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const double bv = b[(int64_t)row * K + q];
+            acc[q] = bv - d * x[(int64_t)row * K + q];
+            if (INIT) bb[q] += bv * bv;
+        }
+        const int32_t* cp = col + m.off + lane;
+        const double* vp = sval + m.off + lane;
+        for (int k = 0; k < m.width; k++) {
+            const int c = ldg(cp + k * 32);
+            const double v = ldg(vp + k * 32);
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[q] -= v * ldg(x + (int64_t)c * K + q);
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            rr[q] += acc[q] * acc[q];
+            if (R32) r32[(int64_t)row * K + q] = (float)acc[q];
+        }
+    }
+    __shared__ double red[kWarps][2 * K];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            rr[q] += __shfl_xor_sync(0xffffffffu, rr[q], o);
+            bb[q] += __shfl_xor_sync(0xffffffffu, bb[q], o);
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            red[wid][q] = rr[q];
+            red[wid][K + q] = bb[q];
+        }
+    __syncthreads();
+    if (threadIdx.x < 2 * K) {
+        double s = 0.0;
+        for (int w = 0; w < kWarps; w++) s += red[w][threadIdx.x];
+        partials[(int64_t)blockIdx.x * 2 * K + threadIdx.x] = s;
+    }
+}
+
+// The same for a dense level-0 matrix (single-level hierarchy): a warp per row.
+template <int K, bool INIT, bool R32>
+__global__ void __launch_bounds__(kThreads) resnorm_dense(int n, const double* __restrict__ A,
+                                                          const double* __restrict__ b, const double* __restrict__ x,
+                                                          double* __restrict__ partials, float* __restrict__ r32) {
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    double rr[K], bb[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) rr[q] = bb[q] = 0.0;
+    for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += gridDim.x * kWarps) {
+        double acc[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const double a = A[(int64_t)i * n + j];
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[q] += a * x[(int64_t)j * K + q];
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            const double bv = b[(int64_t)i * K + q];
+            const double rv = bv - acc[q];
+            if (lane == 0) {
+                rr[q] += rv * rv;
+                if (INIT) bb[q] += bv * bv;
+                if (R32) r32[(int64_t)i * K + q] = (float)rv;
+            }
+        }
+    }
+    __shared__ double red[kWarps][2 * K];
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            red[wid][q] = rr[q];
+            red[wid][K + q] = bb[q];
+        }
+    __syncthreads();
+    if (threadIdx.x < 2 * K) {
+        double s = 0.0;
+        for (int w = 0; w < kWarps; w++) s += red[w][threadIdx.x];
+        partials[(int64_t)blockIdx.x * 2 * K + threadIdx.x] = s;
+    }
+}
+
+// Final reduction and stopping test.  `init`: before the first cycle (records
+// ||b|| and rel0); otherwise after a cycle.  Sets the WHILE condition of the
+// solve graph: continue while rel > rtol, finite, and cycles < max_cycles.
+template <int K>
+__global__ void norm_final(const double* __restrict__ partials, int nblocks, SolveState* __restrict__ st,
+                           cudaGraphConditionalHandle hnd, int init, double rtol, int max_cycles, int use_cond) {
+    __shared__ double red[kThreads][2 * K];
+    double acc[2 * K];
+#pragma unroll
+    for (int q = 0; q < 2 * K; q++) acc[q] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 2 * K; q++) acc[q] += partials[(int64_t)b * 2 * K + q];
+#pragma unroll
+    for (int q = 0; q < 2 * K; q++) red[threadIdx.x][q] = acc[q];
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 2 * K; q++) red[threadIdx.x][q] += red[threadIdx.x + w][q];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    if (init)
+        for (int q = 0; q < K; q++) st->bnorm2[q] = red[0][K + q];
+    double rel = 0.0;
+    for (int q = 0; q < K; q++) {
+        const double bn = st->bnorm2[q];
+        const double rq = bn > 0.0 ? sqrt(red[0][q] / bn) : sqrt(red[0][q]);
+        rel = (rq > rel || rq != rq) ? rq : rel;
+    }
+    if (init) {
+        st->rel0 = rel;
+        st->cycles = 0;
+    } else {
+        st->cycles += 1;
+    }
+    st->rel = rel;
+    const bool finite = isfinite(rel);
+    const bool converged = finite && rel <= rtol;
+    const bool more = finite && !converged && st->cycles < max_cycles;
+    st->status = converged ? SMG_OK : (!finite ? SMG_ERR_DIVERGED : (more ? -1 : SMG_ERR_NOT_CONVERGED));
+    if (use_cond) cudaGraphSetConditional(hnd, more ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Per-frame update kernels
+
+// Per face: cotangent of the angle at each corner and the area.
+__global__ void face_geom(int64_t nf, const int32_t* __restrict__ F, const double* __restrict__ V,
+                          double* __restrict__ fg) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    double p[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const int64_t v = F[3 * f + c];
+#pragma unroll
+        for (int d = 0; d < 3; d++) p[c][d] = V[3 * v + d];
+    }
+    double e1[3], e2[3], cr[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        e1[d] = p[1][d] - p[0][d];
+        e2[d] = p[2][d] - p[0][d];
+    }
+    cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double dbl = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);  // twice the area
+    const double inv = 1.0 / dbl;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double* a = p[c];
+        const double* u = p[(c + 1) % 3];
+        const double* w = p[(c + 2) % 3];
+        const double dot = (u[0] - a[0]) * (w[0] - a[0]) + (u[1] - a[1]) * (w[1] - a[1]) + (u[2] - a[2]) * (w[2] - a[2]);
+        fg[4 * f + c] = dot * inv;  // |e1 x e2| is the same at every corner
+    }
+    fg[4 * f + 3] = 0.5 * dbl;
+}
+
+// Diagonal of the cotan Laplacian (positive semi-definite sign) and the lumped
+// mass: L_ii = sum over incident faces of (cot of the two other corners) / 2,
+// M_ii = sum of incident face areas / 3.
+__global__ void asm_diag(int64_t n, int64_t dstride, const int32_t* __restrict__ inc_ptr,
+                         const int32_t* __restrict__ inc_code, const double* __restrict__ fg,
+                         double* __restrict__ Lflat, double* __restrict__ M) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double ld = 0.0, m = 0.0;
+    for (int k = inc_ptr[p]; k < inc_ptr[p + 1]; k++) {
+        const int code = inc_code[k];
+        const int64_t f = code / 3;
+        const int c = code - 3 * (code / 3);
+        ld += 0.5 * (fg[4 * f + (c + 1) % 3] + fg[4 * f + (c + 2) % 3]);
+        m += fg[4 * f + 3] / 3.0;
+    }
+    Lflat[p * dstride] = ld;
+    M[p] = m;
+}
+
+// Off-diagonal cotan weights: L_ij = -(cot a + cot b) / 2 over the corners
+// opposite the edge ij (one corner on a boundary edge).
+__global__ void asm_off(int64_t nflat, int64_t first, int64_t dense_n, const int32_t* __restrict__ opp0,
+                        const int32_t* __restrict__ opp1, const double* __restrict__ fg, double* __restrict__ Lflat) {
+    const int64_t e = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nflat) return;
+    if (dense_n > 0 && e / dense_n == e % dense_n) return;
+    const int a = opp0[e], b = opp1[e];
+    double s = 0.0;
+    if (a >= 0) s += fg[4 * (int64_t)(a / 3) + a % 3];
+    if (b >= 0) s += fg[4 * (int64_t)(b / 3) + b % 3];
+    Lflat[e] = -0.5 * s;
+}
+
+// A = t L + M on the flat layout.
+__global__ void combine(int64_t nflat, int64_t n, int64_t dense_n, double t, const double* __restrict__ Lflat,
+                        const double* __restrict__ M, double* __restrict__ vals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nflat) return;
+    double v = t * Lflat[e];
+    if (dense_n > 0) {
+        if (e / dense_n == e % dense_n) v += M[e / dense_n];
+    } else if (e < n) {
+        v += M[e];
+    }
+    vals[e] = v;
+}
+
+// User-supplied level-0 values (natural CSR) scattered to the flat layout.
+__global__ void scatter_user(int64_t nflat, const int64_t* __restrict__ map, const double* __restrict__ user,
+                             double* __restrict__ vals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nflat) return;
+    const int64_t k = map[e];
+    vals[e] = k >= 0 ? user[k] : 0.0;
+}
+
+// Numeric Galerkin product A_{h+1} = P^T A_h P on the precomputed pattern: each
+// coarse entry gathers its fixed list of (fine entry, P_iI P_jJ) pairs.
+__global__ void galerkin(int64_t nflat_c, const int64_t* __restrict__ gp, const int32_t* __restrict__ src,
+                         const double* __restrict__ w, const double* __restrict__ fine, double* __restrict__ coarse) {
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nflat_c) return;
+    double acc = 0.0;
+    for (int64_t k = gp[d]; k < gp[d + 1]; k++) acc += w[k] * ldg(fine + src[k]);
+    coarse[d] = acc;
+}
+
+// Reciprocal diagonal and the binary32 copies used by the mixed-precision cycle.
+__global__ void prep_level(int64_t nflat, int64_t n, const double* __restrict__ vals, double* __restrict__ dinv,
+                           float* __restrict__ vals32, float* __restrict__ dinv32) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nflat) return;
+    vals32[e] = (float)vals[e];
+    if (e < n) {
+        const double di = 1.0 / vals[e];
+        dinv[e] = di;
+        dinv32[e] = (float)di;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Permutation between the caller's unknown order and the colour-major order.
+template <typename T>
+__global__ void gather_rows(int64_t n, int K, const int32_t* __restrict__ perm, const T* __restrict__ src,
+                            T* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * K) return;
+    const int64_t p = e / K, q = e - p * K;
+    dst[e] = src[(int64_t)perm[p] * K + q];
+}
+template <typename T>
+__global__ void scatter_rows(int64_t n, int K, const int32_t* __restrict__ perm, const T* __restrict__ src,
+                             T* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * K) return;
+    const int64_t p = e / K, q = e - p * K;
+    dst[(int64_t)perm[p] * K + q] = src[e];
+}
+
+// Iterative refinement update x <- x + d (binary32 correction, binary64 iterate).
+__global__ void ir_update(int64_t m, const float* __restrict__ d, double* __restrict__ x) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    x[e] += (double)d[e];
+}
+
+// y = M x with the lumped mass (permuted rows) written in the caller's order.
+__global__ void apply_mass(int64_t n, int K, const int32_t* __restrict__ perm, const double* __restrict__ M,
+                           const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * K) return;
+    const int64_t p = e / K, q = e - p * K;
+    const int64_t u = perm[p];
+    y[u * K + q] = M[p] * x[u * K + q];
+}
+
+}  // namespace kern
+}  // namespace smg

@@ -1,0 +1,519 @@
+// Geometry-only setup: level loop, Dirichlet reduction, symbolic Galerkin
+// patterns, Alg. 3 colourings and the device-ready layouts.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "plan.hpp"
+
+namespace smg {
+
+static int validate_mesh(const double* V, int64_t n, const int32_t* F, int64_t m, std::string& err) {
+    if (!V || !F || n < 3 || m < 1 || n > (int64_t)INT32_MAX / 4 || m > (int64_t)INT32_MAX / 4) {
+        err = "invalid mesh sizes or null arrays";
+        return SMG_ERR_INVALID_ARG;
+    }
+    for (int64_t k = 0; k < 3 * n; k++)
+        if (!std::isfinite(V[k])) {
+            err = "non-finite vertex position";
+            return SMG_ERR_INVALID_ARG;
+        }
+    std::vector<int64_t> he;  // directed edges a*n+b
+    he.reserve(3 * m);
+    for (int64_t f = 0; f < m; f++) {
+        int32_t a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n) {
+            err = "face index out of range";
+            return SMG_ERR_INVALID_ARG;
+        }
+        if (a == b || b == c || c == a) {
+            err = "degenerate face (repeated vertex)";
+            return SMG_ERR_NONMANIFOLD;
+        }
+        he.push_back((int64_t)a * n + b);
+        he.push_back((int64_t)b * n + c);
+        he.push_back((int64_t)c * n + a);
+    }
+    std::sort(he.begin(), he.end());
+    for (size_t k = 1; k < he.size(); k++)
+        if (he[k] == he[k - 1]) {
+            err = "directed edge used twice: non-manifold or inconsistently oriented mesh";
+            return SMG_ERR_NONMANIFOLD;
+        }
+    return SMG_OK;
+}
+
+int build_plan(const double* V, int64_t n, const int32_t* F, int64_t m, const uint8_t* mask,
+               const smg_options& o, Plan& p, std::string& err) {
+    int st = validate_mesh(V, n, F, m, err);
+    if (st) return st;
+    if (!(o.ratio > 0.0 && o.ratio < 1.0) || o.mu_pre < 0 || o.mu_post < 0) {
+        err = "invalid options";
+        return SMG_ERR_INVALID_ARG;
+    }
+    p.opts = o;
+    p.meshes.clear();
+    p.praw.clear();
+    p.stats.clear();
+    MeshData m0;
+    m0.V.assign(V, V + 3 * n);
+    m0.F.assign(F, F + 3 * m);
+    p.meshes.push_back(std::move(m0));
+    p.known.assign(n, 0);
+    if (mask)
+        for (int64_t v = 0; v < n; v++) p.known[v] = mask[v] ? 1 : 0;
+    // level loop (Sec. 5: ratio 0.25 per level, coarsest no smaller than 500)
+    for (;;) {
+        const MeshData& cur = p.meshes.back();
+        int64_t nc = cur.n();
+        if (o.max_levels > 0 && (int64_t)p.meshes.size() >= o.max_levels) break;
+        int64_t target = (int64_t)std::nearbyint(o.ratio * (double)nc);
+        if (o.max_coarse > 0) {
+            if (nc <= o.max_coarse) break;
+        } else if (target < o.min_coarse) {
+            break;
+        }
+        if (target < 4 || target >= nc) break;
+        MeshData next;
+        ProlongationRaw P;
+        DecimationStats ds;
+        if (decimate_level(cur, target, next, P, ds, err) != 0) return SMG_ERR_DECIMATION;
+        if (next.n() >= nc) break;
+        p.meshes.push_back(std::move(next));
+        p.praw.push_back(std::move(P));
+        p.stats.push_back(ds);
+    }
+    return finalize_plan(p, err);
+}
+
+// --------------------------------------------------------------------------
+// symbolic P^T S P
+static void galerkin_pattern(int64_t nf, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                             const std::vector<int32_t>& pidx, int64_t nc, std::vector<int64_t>& crp,
+                             std::vector<int32_t>& cci) {
+    std::vector<int64_t> tp(nc + 1, 0);
+    for (int64_t i = 0; i < nf; i++)
+        for (int a = 0; a < 3; a++)
+            if (pidx[3 * i + a] >= 0) tp[pidx[3 * i + a] + 1]++;
+    for (int64_t I = 0; I < nc; I++) tp[I + 1] += tp[I];
+    std::vector<int32_t> trow(tp[nc]);
+    std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+    for (int64_t i = 0; i < nf; i++)
+        for (int a = 0; a < 3; a++)
+            if (pidx[3 * i + a] >= 0) trow[fill[pidx[3 * i + a]]++] = (int32_t)i;
+    std::vector<int64_t> mark(nc, -1);
+    std::vector<int32_t> row;
+    crp.assign(nc + 1, 0);
+    cci.clear();
+    for (int64_t I = 0; I < nc; I++) {
+        row.clear();
+        for (int64_t t = tp[I]; t < tp[I + 1]; t++) {
+            int32_t i = trow[t];
+            for (int64_t q = rp[i]; q < rp[i + 1]; q++) {
+                int32_t j = ci[q];
+                for (int b = 0; b < 3; b++) {
+                    int32_t J = pidx[3 * j + b];
+                    if (J >= 0 && mark[J] != I) {
+                        mark[J] = I;
+                        row.push_back(J);
+                    }
+                }
+            }
+        }
+        std::sort(row.begin(), row.end());
+        cci.insert(cci.end(), row.begin(), row.end());
+        crp[I + 1] = (int64_t)cci.size();
+    }
+}
+
+static int64_t csr_find(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, int64_t r, int32_t c) {
+    auto b = ci.begin() + rp[r], e = ci.begin() + rp[r + 1];
+    auto it = std::lower_bound(b, e, c);
+    if (it == e || *it != c) return -1;
+    return (int64_t)(it - ci.begin());
+}
+
+// slot of (I, J), I != J, in the SELL layout of level `lv` (permuted indices), -1 if absent
+static int64_t sell_find(const LevelPlan& lv, const std::vector<int32_t>& slice_of_row, int32_t I, int32_t J) {
+    const SliceMeta& s = lv.slices[slice_of_row[I]];
+    int lane = I - s.row0;
+    int lo = 0, hi = s.width;
+    while (lo < hi) {  // columns of a row ascend; padding (the row itself) sorts last
+        int mid = (lo + hi) / 2;
+        int32_t c = lv.sell_col[(size_t)s.off + (size_t)mid * kSlice + lane];
+        bool pad = (c == I);
+        if (!pad && c < J) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < s.width) {
+        int32_t c = lv.sell_col[(size_t)s.off + (size_t)lo * kSlice + lane];
+        if (c == J && c != I) return (int64_t)s.off + (int64_t)lo * kSlice + lane;
+    }
+    return -1;
+}
+
+int finalize_plan(Plan& p, std::string& err) {
+    const int H = (int)p.meshes.size() - 1;
+    const MeshData& m0 = p.meshes[0];
+    const int64_t n0 = m0.n();
+    p.L.assign(H + 1, LevelPlan());
+
+    // ---- Dirichlet reduction (App. "Dirichlet Boundary Conditions")
+    std::vector<int32_t> unk_of(n0, -1);
+    p.unknowns.clear();
+    for (int64_t v = 0; v < n0; v++)
+        if (!p.known[v]) {
+            unk_of[v] = (int32_t)p.unknowns.size();
+            p.unknowns.push_back((int32_t)v);
+        }
+    if (p.unknowns.empty()) {
+        err = "every vertex is Dirichlet-known";
+        return SMG_ERR_INVALID_ARG;
+    }
+    std::vector<int32_t> kept_of;
+    p.kept1.clear();
+    if (H >= 1) {
+        const ProlongationRaw& P1 = p.praw[0];
+        std::vector<char> used(P1.n_coarse, 0);
+        for (int32_t v : p.unknowns)
+            for (int a = 0; a < 3; a++)
+                if (P1.idx[3 * v + a] >= 0 && P1.w[3 * v + a] > 0) used[P1.idx[3 * v + a]] = 1;
+        kept_of.assign(P1.n_coarse, -1);
+        for (int64_t c = 0; c < P1.n_coarse; c++)
+            if (used[c]) {
+                kept_of[c] = (int32_t)p.kept1.size();
+                p.kept1.push_back((int32_t)c);
+            }
+    }
+    // level sizes and natural reduced prolongations
+    for (int l = 0; l <= H; l++) {
+        LevelPlan& lv = p.L[l];
+        lv.coarsest = (l == H);
+        lv.n = l == 0 ? (int64_t)p.unknowns.size() : (l == 1 ? (int64_t)p.kept1.size() : p.meshes[l].n());
+    }
+    for (int l = 0; l < H; l++) {
+        LevelPlan& lv = p.L[l];
+        const ProlongationRaw& P = p.praw[l];
+        lv.pn_idx.assign(3 * lv.n, -1);
+        lv.pn_w.assign(3 * lv.n, 0.0);
+        for (int64_t r = 0; r < lv.n; r++) {
+            int64_t src = l == 0 ? p.unknowns[r] : (l == 1 ? p.kept1[r] : r);
+            int k = 0;
+            for (int a = 0; a < 3; a++) {
+                int32_t c = P.idx[3 * src + a];
+                double w = P.w[3 * src + a];
+                if (c < 0 || !(w > 0)) continue;
+                int32_t cc = l == 0 ? kept_of[c] : c;
+                if (cc < 0) {
+                    err = "internal: kept column lookup failed";
+                    return SMG_ERR_DECIMATION;
+                }
+                lv.pn_idx[3 * r + k] = cc;
+                lv.pn_w[3 * r + k] = w;
+                k++;
+            }
+            if (k == 0) {
+                err = "prolongation row without weights";
+                return SMG_ERR_DECIMATION;
+            }
+        }
+        std::vector<char> hit(p.L[l + 1].n, 0);
+        for (int64_t r = 0; r < lv.n; r++)
+            for (int a = 0; a < 3; a++)
+                if (lv.pn_idx[3 * r + a] >= 0) hit[lv.pn_idx[3 * r + a]] = 1;
+        for (int64_t c = 0; c < p.L[l + 1].n; c++)
+            if (!hit[c]) {
+                err = "coarse vertex without support at level " + std::to_string(l + 1) +
+                      " (too many Dirichlet-known vertices)";
+                return SMG_ERR_DECIMATION;
+            }
+    }
+
+    // ---- symbolic patterns
+    {
+        LevelPlan& lv = p.L[0];
+        std::vector<std::vector<int32_t>> adj(lv.n);
+        for (int64_t f = 0; f < m0.m(); f++)
+            for (int c = 0; c < 3; c++) {
+                int32_t a = unk_of[m0.F[3 * f + c]], b = unk_of[m0.F[3 * f + (c + 1) % 3]];
+                if (a >= 0 && b >= 0) {
+                    adj[a].push_back(b);
+                    adj[b].push_back(a);
+                }
+            }
+        lv.rowptr.assign(lv.n + 1, 0);
+        lv.col.clear();
+        for (int64_t r = 0; r < lv.n; r++) {
+            auto& a = adj[r];
+            a.push_back((int32_t)r);
+            std::sort(a.begin(), a.end());
+            a.erase(std::unique(a.begin(), a.end()), a.end());
+            lv.col.insert(lv.col.end(), a.begin(), a.end());
+            lv.rowptr[r + 1] = (int64_t)lv.col.size();
+        }
+    }
+    for (int l = 0; l < H; l++)
+        galerkin_pattern(p.L[l].n, p.L[l].rowptr, p.L[l].col, p.L[l].pn_idx, p.L[l + 1].n, p.L[l + 1].rowptr,
+                         p.L[l + 1].col);
+    if (p.L[H].n > 16384) {
+        err = "coarsest level too large for the dense factor (" + std::to_string(p.L[H].n) + " > 16384)";
+        return SMG_ERR_DECIMATION;
+    }
+
+    // ---- colouring, permutation and SELL-32 layout per level
+    for (int l = 0; l <= H; l++) {
+        LevelPlan& lv = p.L[l];
+        const int64_t n = lv.n;
+        lv.perm.resize(n);
+        lv.iperm.resize(n);
+        if (lv.coarsest) {
+            std::iota(lv.perm.begin(), lv.perm.end(), 0);
+            std::iota(lv.iperm.begin(), lv.iperm.end(), 0);
+            lv.ncolours = 0;
+            lv.colour.clear();
+            lv.nflat = n * n;
+            continue;
+        }
+        lv.ncolours = greedy_colouring(n, lv.rowptr, lv.col, lv.colour);
+        std::vector<int32_t> len(n);
+        for (int64_t r = 0; r < n; r++) len[r] = (int32_t)(lv.rowptr[r + 1] - lv.rowptr[r] - 1);
+        std::iota(lv.perm.begin(), lv.perm.end(), 0);
+        // colour classes one after another; longer rows first inside a class so a
+        // warp's 32 rows have similar lengths (order inside a class does not change
+        // the sweep: no two rows of a class are coupled)
+        std::stable_sort(lv.perm.begin(), lv.perm.end(), [&](int32_t a, int32_t b) {
+            if (lv.colour[a] != lv.colour[b]) return lv.colour[a] < lv.colour[b];
+            return len[a] > len[b];
+        });
+        for (int64_t q = 0; q < n; q++) lv.iperm[lv.perm[q]] = (int32_t)q;
+        lv.colour_row.assign(lv.ncolours + 1, 0);
+        for (int64_t r = 0; r < n; r++) lv.colour_row[lv.colour[r] + 1]++;
+        for (int c = 0; c < lv.ncolours; c++) lv.colour_row[c + 1] += lv.colour_row[c];
+        lv.slices.clear();
+        lv.colour_slice.assign(lv.ncolours + 1, 0);
+        int64_t off = 0;
+        for (int c = 0; c < lv.ncolours; c++) {
+            for (int32_t r0 = lv.colour_row[c]; r0 < lv.colour_row[c + 1]; r0 += kSlice) {
+                SliceMeta s;
+                s.row0 = r0;
+                s.nrows = std::min(kSlice, lv.colour_row[c + 1] - r0);
+                s.width = 0;
+                for (int k = 0; k < s.nrows; k++) s.width = std::max(s.width, len[lv.perm[r0 + k]]);
+                if (off > (int64_t)INT32_MAX - (int64_t)s.width * kSlice) {
+                    err = "level too large for 32-bit slot offsets";
+                    return SMG_ERR_INVALID_ARG;
+                }
+                s.off = (int32_t)off;
+                off += (int64_t)s.width * kSlice;
+                lv.slices.push_back(s);
+            }
+            lv.colour_slice[c + 1] = (int32_t)lv.slices.size();
+        }
+        lv.nslots = off;
+        lv.sbase = (n + kSlice - 1) / kSlice * kSlice;
+        lv.nflat = lv.sbase + off;
+        lv.sell_col.assign(off, 0);
+        std::vector<int32_t> cols;
+        for (const SliceMeta& s : lv.slices)
+            for (int lane = 0; lane < kSlice; lane++) {
+                int32_t prow = s.row0 + (lane < s.nrows ? lane : 0);
+                cols.clear();
+                if (lane < s.nrows) {
+                    int32_t r = lv.perm[prow];
+                    for (int64_t q = lv.rowptr[r]; q < lv.rowptr[r + 1]; q++)
+                        if (lv.col[q] != r) cols.push_back(lv.iperm[lv.col[q]]);
+                    std::sort(cols.begin(), cols.end());
+                }
+                for (int k = 0; k < s.width; k++)
+                    lv.sell_col[(size_t)s.off + (size_t)k * kSlice + lane] = k < (int)cols.size() ? cols[k] : prow;
+            }
+    }
+
+    // ---- flat index -> natural CSR position
+    for (int l = 0; l <= H; l++) {
+        LevelPlan& lv = p.L[l];
+        lv.flat_to_csr.assign(lv.nflat, -1);
+        if (lv.coarsest) {
+            for (int64_t I = 0; I < lv.n; I++)
+                for (int64_t q = lv.rowptr[I]; q < lv.rowptr[I + 1]; q++) lv.flat_to_csr[I * lv.n + lv.col[q]] = q;
+            continue;
+        }
+        for (int64_t pr = 0; pr < lv.n; pr++) lv.flat_to_csr[pr] = csr_find(lv.rowptr, lv.col, lv.perm[pr], lv.perm[pr]);
+        for (const SliceMeta& s : lv.slices)
+            for (int lane = 0; lane < s.nrows; lane++) {
+                int32_t pr = s.row0 + lane;
+                for (int k = 0; k < s.width; k++) {
+                    int64_t slot = (int64_t)s.off + (int64_t)k * kSlice + lane;
+                    int32_t pc = lv.sell_col[slot];
+                    if (pc == pr) continue;
+                    lv.flat_to_csr[lv.sbase + slot] = csr_find(lv.rowptr, lv.col, lv.perm[pr], lv.perm[pc]);
+                }
+            }
+    }
+
+    // ---- permuted prolongation, restriction and Galerkin plans
+    for (int l = 0; l < H; l++) {
+        LevelPlan& lv = p.L[l];
+        LevelPlan& nx = p.L[l + 1];
+        const int64_t n = lv.n, nc = nx.n;
+        lv.p_idx.assign(3 * n, 0);
+        lv.p_w.assign(3 * n, 0.0);
+        for (int64_t pr = 0; pr < n; pr++) {
+            int32_t r = lv.perm[pr];
+            int32_t first = nx.iperm[lv.pn_idx[3 * r]];
+            for (int a = 0; a < 3; a++) {
+                int32_t c = lv.pn_idx[3 * r + a];
+                lv.p_idx[a * n + pr] = c >= 0 ? nx.iperm[c] : first;
+                lv.p_w[a * n + pr] = c >= 0 ? lv.pn_w[3 * r + a] : 0.0;
+            }
+        }
+        lv.pt_ptr.assign(nc + 1, 0);
+        for (int64_t pr = 0; pr < n; pr++)
+            for (int a = 0; a < 3; a++)
+                if (lv.p_w[a * n + pr] != 0.0) lv.pt_ptr[lv.p_idx[a * n + pr] + 1]++;
+        for (int64_t I = 0; I < nc; I++) lv.pt_ptr[I + 1] += lv.pt_ptr[I];
+        lv.pt_row.assign(lv.pt_ptr[nc], 0);
+        lv.pt_w.assign(lv.pt_ptr[nc], 0.0);
+        {
+            std::vector<int32_t> fill(lv.pt_ptr.begin(), lv.pt_ptr.end() - 1);
+            for (int64_t pr = 0; pr < n; pr++)
+                for (int a = 0; a < 3; a++)
+                    if (lv.p_w[a * n + pr] != 0.0) {
+                        int32_t I = lv.p_idx[a * n + pr];
+                        lv.pt_row[fill[I]] = (int32_t)pr;
+                        lv.pt_w[fill[I]] = lv.p_w[a * n + pr];
+                        fill[I]++;
+                    }
+        }
+        // Galerkin contributions: fine entry (p, q) with value a_pq adds
+        // P[p, I] a_pq P[q, J] to coarse (I, J) for every weight pair.
+        std::vector<int32_t> nx_slice_of_row;
+        if (!nx.coarsest) {
+            nx_slice_of_row.assign(nc, 0);
+            for (size_t s = 0; s < nx.slices.size(); s++)
+                for (int k = 0; k < nx.slices[s].nrows; k++) nx_slice_of_row[nx.slices[s].row0 + k] = (int32_t)s;
+        }
+        auto dst_of = [&](int32_t I, int32_t J) -> int64_t {
+            if (nx.coarsest) return (int64_t)I * nc + J;
+            if (I == J) return I;
+            int64_t s = sell_find(nx, nx_slice_of_row, I, J);
+            return s < 0 ? -1 : nx.sbase + s;
+        };
+        lv.g_ptr.assign(nx.nflat + 1, 0);
+        bool bad = false;
+        for (int pass = 0; pass < 2 && !bad; pass++) {
+            std::vector<int64_t> fill;
+            if (pass == 1) {
+                for (int64_t d = 0; d < nx.nflat; d++) lv.g_ptr[d + 1] += lv.g_ptr[d];
+                if (lv.g_ptr[nx.nflat] > (int64_t)INT32_MAX) {
+                    err = "Galerkin plan too large";
+                    return SMG_ERR_INVALID_ARG;
+                }
+                lv.g_src.assign(lv.g_ptr[nx.nflat], 0);
+                lv.g_w.assign(lv.g_ptr[nx.nflat], 0.0);
+                fill.assign(lv.g_ptr.begin(), lv.g_ptr.end() - 1);
+            }
+            auto emit = [&](int32_t pr, int32_t pc, int64_t e) {
+                for (int a = 0; a < 3; a++) {
+                    double wa = lv.p_w[a * n + pr];
+                    if (wa == 0.0) continue;
+                    int32_t I = lv.p_idx[a * n + pr];
+                    for (int b = 0; b < 3; b++) {
+                        double wb = lv.p_w[b * n + pc];
+                        if (wb == 0.0) continue;
+                        int64_t d = dst_of(I, lv.p_idx[b * n + pc]);
+                        if (d < 0) {
+                            bad = true;
+                            return;
+                        }
+                        if (pass == 0) lv.g_ptr[d + 1]++;
+                        else {
+                            lv.g_src[fill[d]] = (int32_t)e;
+                            lv.g_w[fill[d]] = wa * wb;
+                            fill[d]++;
+                        }
+                    }
+                }
+            };
+            for (int64_t pr = 0; pr < n; pr++) emit((int32_t)pr, (int32_t)pr, pr);
+            for (const SliceMeta& s : lv.slices)
+                for (int lane = 0; lane < s.nrows; lane++)
+                    for (int k = 0; k < s.width; k++) {
+                        int64_t slot = (int64_t)s.off + (int64_t)k * kSlice + lane;
+                        int32_t pc = lv.sell_col[slot];
+                        if (pc == s.row0 + lane) continue;
+                        emit(s.row0 + lane, pc, lv.sbase + slot);
+                    }
+        }
+        if (bad) {
+            err = "internal: Galerkin destination missing from the symbolic pattern";
+            return SMG_ERR_DECIMATION;
+        }
+    }
+
+    // ---- level-0 assembly plan
+    AssemblyPlan& A = p.asmb;
+    const LevelPlan& l0 = p.L[0];
+    A.nv = n0;
+    A.nf = m0.m();
+    A.F = m0.F;
+    A.row_vertex.resize(l0.n);
+    for (int64_t pr = 0; pr < l0.n; pr++) A.row_vertex[pr] = p.unknowns[l0.perm[pr]];
+    {
+        std::vector<int32_t> cnt(n0 + 1, 0);
+        for (int64_t f = 0; f < A.nf; f++)
+            for (int c = 0; c < 3; c++) cnt[A.F[3 * f + c] + 1]++;
+        for (int64_t v = 0; v < n0; v++) cnt[v + 1] += cnt[v];
+        std::vector<int32_t> vc(cnt[n0]);
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int64_t f = 0; f < A.nf; f++)
+            for (int c = 0; c < 3; c++) vc[fill[A.F[3 * f + c]]++] = (int32_t)(3 * f + c);
+        A.inc_ptr.assign(l0.n + 1, 0);
+        A.inc_code.clear();
+        for (int64_t pr = 0; pr < l0.n; pr++) {
+            int32_t v = A.row_vertex[pr];
+            for (int32_t q = cnt[v]; q < cnt[v + 1]; q++) A.inc_code.push_back(vc[q]);
+            A.inc_ptr[pr + 1] = (int32_t)A.inc_code.size();
+        }
+    }
+    {
+        // edge -> corners opposite to it
+        std::vector<std::pair<int64_t, int32_t>> eo;
+        eo.reserve(3 * A.nf);
+        for (int64_t f = 0; f < A.nf; f++)
+            for (int c = 0; c < 3; c++) {
+                int64_t a = A.F[3 * f + (c + 1) % 3], b = A.F[3 * f + (c + 2) % 3];
+                eo.push_back({std::min(a, b) * n0 + std::max(a, b), (int32_t)(3 * f + c)});
+            }
+        std::sort(eo.begin(), eo.end());
+        auto opp_of = [&](int64_t a, int64_t b, int32_t& o0, int32_t& o1) {
+            int64_t key = std::min(a, b) * n0 + std::max(a, b);
+            auto it = std::lower_bound(eo.begin(), eo.end(), std::make_pair(key, (int32_t)-1));
+            o0 = o1 = -1;
+            if (it != eo.end() && it->first == key) { o0 = it->second; ++it; }
+            if (it != eo.end() && it->first == key) { o1 = it->second; }
+        };
+        A.opp0.assign(l0.nflat, -1);
+        A.opp1.assign(l0.nflat, -1);
+        if (l0.coarsest) {
+            for (int64_t I = 0; I < l0.n; I++)
+                for (int64_t J = 0; J < l0.n; J++)
+                    if (I != J) opp_of(A.row_vertex[I], A.row_vertex[J], A.opp0[I * l0.n + J], A.opp1[I * l0.n + J]);
+        } else {
+            for (const SliceMeta& s : l0.slices)
+                for (int lane = 0; lane < s.nrows; lane++)
+                    for (int k = 0; k < s.width; k++) {
+                        int64_t slot = (int64_t)s.off + (int64_t)k * kSlice + lane;
+                        int32_t pc = l0.sell_col[slot];
+                        if (pc == s.row0 + lane) continue;
+                        opp_of(A.row_vertex[s.row0 + lane], A.row_vertex[pc], A.opp0[l0.sbase + slot],
+                               A.opp1[l0.sbase + slot]);
+                    }
+        }
+        A.flat_to_user = l0.flat_to_csr;
+    }
+    return SMG_OK;
+}
+
+}  // namespace smg

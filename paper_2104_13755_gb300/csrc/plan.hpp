@@ -1,0 +1,93 @@
+// Internal: the geometry-only plan and its device-ready layouts.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/smg.h"
+#include "smg_host.hpp"
+
+namespace smg {
+
+constexpr int kSlice = 32;  // rows per SELL slice (one warp)
+
+// Per-slice header of the SELL-32 off-diagonal storage.
+struct SliceMeta {
+    int32_t row0;   // first (permuted) row of the slice
+    int32_t nrows;  // rows in the slice (<= 32; the last slice of a colour may be short)
+    int32_t width;  // padded off-diagonal entries per row
+    int32_t off;    // first slot; entry k of lane r sits at off + k * 32 + r
+};
+
+struct LevelPlan {
+    int64_t n = 0;
+    bool coarsest = false;
+    // natural-order symbolic pattern (sorted, diagonal included)
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> col;
+    // Alg. 3 colouring (natural numbering), permutation new -> natural and inverse
+    int32_t ncolours = 0;
+    std::vector<int32_t> colour, perm, iperm;
+    // permuted layout: colour classes and SELL-32 off-diagonal slots
+    std::vector<int32_t> colour_row;    // ncolours + 1
+    std::vector<int32_t> colour_slice;  // ncolours + 1
+    std::vector<SliceMeta> slices;
+    std::vector<int32_t> sell_col;      // permuted column of every slot (padding: the row itself)
+    int64_t nslots = 0;
+    // flat value array of A_l: [diag (n, padded to sbase) | slots (nslots)], or dense
+    // n x n at the coarsest; slot s lives at flat index sbase + s
+    int64_t sbase = 0;
+    int64_t nflat = 0;
+    // natural-order reduced prolongation to the next level (3 per row, -1 unused)
+    std::vector<int32_t> pn_idx;
+    std::vector<double> pn_w;
+    // permuted prolongation (slot-major [3][n]) and restriction CSR (rows = next level)
+    std::vector<int32_t> p_idx;
+    std::vector<double> p_w;
+    std::vector<int32_t> pt_ptr, pt_row;
+    std::vector<double> pt_w;
+    // Galerkin plan: next-level flat entry d = sum over k in [g_ptr[d], g_ptr[d+1]) of
+    // g_w[k] * flat_this[g_src[k]]
+    std::vector<int64_t> g_ptr;
+    std::vector<int32_t> g_src;
+    std::vector<double> g_w;
+    // flat index -> position in the natural CSR pattern (for read-back)
+    std::vector<int64_t> flat_to_csr;
+};
+
+struct AssemblyPlan {
+    int64_t nv = 0, nf = 0;            // all mesh vertices, faces
+    std::vector<int32_t> F;            // 3 nf
+    std::vector<int32_t> row_vertex;   // permuted level-0 row -> mesh vertex
+    std::vector<int32_t> inc_ptr;      // incident face corners per permuted row
+    std::vector<int32_t> inc_code;     // face * 3 + corner of the row's vertex
+    std::vector<int32_t> opp0, opp1;   // per slot: face * 3 + corner opposite the edge (-1 none)
+    std::vector<int64_t> flat_to_user; // flat index -> user CSR position (-1 padding)
+};
+
+struct Plan {
+    smg_options opts{};
+    std::vector<MeshData> meshes;          // geometry levels 0..H
+    std::vector<ProlongationRaw> praw;     // praw[l] = P_{l+1}
+    std::vector<DecimationStats> stats;
+    std::vector<uint8_t> known;            // n0
+    std::vector<int32_t> unknowns;         // level-0 natural index -> vertex
+    std::vector<int32_t> kept1;            // level-1 natural index -> mesh-1 vertex
+    std::vector<LevelPlan> L;              // algebraic levels 0..H
+    AssemblyPlan asmb;
+};
+
+// Build the algebraic part (patterns ... assembly plan) from meshes/praw/known.
+int finalize_plan(Plan& p, std::string& err);
+// Build everything from a mesh.
+int build_plan(const double* V, int64_t n, const int32_t* F, int64_t m, const uint8_t* mask,
+               const smg_options& o, Plan& p, std::string& err);
+
+void set_error(const std::string& msg);
+
+}  // namespace smg
+
+struct smg_plan {
+    smg::Plan p;
+};

@@ -1,0 +1,194 @@
+"""CUDA path against the oracle, element by element, through the C ABI.
+
+Tolerances: binary64 kernels differ from the oracle only in summation order,
+so the assembled and Galerkin operators agree to 1e-13 relative and each V-cycle
+iterate to 1e-12 relative (||x_gpu - x_oracle|| / ||x_oracle||).  The mixed form
+is held to 1e-9 relative error against a direct solve."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2104_13755_gb300 as smg  # noqa: E402
+
+CYCLE_TOL = 1e-12
+
+
+class Case:
+    def __init__(self, V, F, t, mask=None, **opts):
+        self.V, self.F, self.t = V, F, t
+        self.plan = smg.Plan(V, F, dirichlet=mask, **opts)
+        self.h = smg.Hierarchy(self.plan, **opts)
+        A = oracle.system_matrix(V, F, t)
+        Ps = [self.plan.prolongation_csr(l) for l in range(1, self.plan.num_levels)]
+        known = mask if mask is not None else np.zeros(V.shape[0], dtype=bool)
+        A, Ps, self.u, _ = oracle.dirichlet_reduce(A, Ps, known)
+        self.A = A
+        self.levels = oracle.build_levels(A, Ps)
+        self.Vd = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+        self.h.update_positions(self.Vd, t)
+        self.n = A.shape[0]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def ico():
+    V, F = synth.perturbed_icosphere(4, seed=0)
+    return Case(V, F, 1e-3, max_levels=3, min_coarse=0)
+
+
+@pytest.fixture(scope="module")
+def torus():
+    V, F = synth.torus(120, 40, seed=2)
+    return Case(V, F, 1e-3, min_coarse=100)
+
+
+@pytest.fixture(scope="module")
+def disk():
+    V, F, bnd = synth.disk(80, seed=4)
+    h = synth.mean_edge_length(V, F)
+    return Case(V, F, h * h, mask=bnd, min_coarse=150)
+
+
+def test_assembly_matches_oracle(ico, disk):
+    for c in (ico, disk):
+        got = c.h.level_matrix(0)
+        ref = c.levels[0].A.data
+        assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+def test_galerkin_matches_oracle(ico, torus, disk):
+    for c in (ico, torus, disk):
+        for l in range(1, c.plan.num_levels):
+            got = c.h.level_matrix(l)
+            ref = c.levels[l].A.data
+            assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), l
+
+
+@pytest.mark.parametrize("name", ["ico", "torus", "disk"])
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_vcycle_parity_every_cycle(name, nrhs, request):
+    c = request.getfixturevalue(name)
+    b = synth.uniform_rhs(c.n, nrhs=nrhs, seed=11)
+    rng = np.random.default_rng(3)
+    x_or = rng.uniform(-1, 1, b.shape)
+    x_gpu = to_dev(x_or.copy())
+    bd = to_dev(b)
+    for k in range(5):
+        x_or = oracle.vcycle(c.levels, 0, np.ascontiguousarray(x_or), b, oracle.Options())
+        c.h.vcycle(bd, x_gpu)
+        assert rel(x_gpu.cpu().numpy(), x_or) <= CYCLE_TOL, k
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 4])
+def test_solve_matches_oracle_and_direct(torus, nrhs):
+    c = torus
+    b = synth.uniform_rhs(c.n, nrhs=nrhs, seed=5)
+    ref = oracle.solve(c.levels, b, opt=oracle.Options(rtol=1e-10))
+    c.h.set_options(rtol=1e-10)
+    x, info = c.h.solve(to_dev(b))
+    assert info["return"] == 0 and info["status"] == 0
+    assert info["cycles"] == ref.cycles
+    assert abs(info["rel_residual"] - ref.history[-1]) <= 1e-6 * ref.history[-1]
+    assert rel(x.cpu().numpy(), ref.x) <= CYCLE_TOL
+    xs = spla.splu(c.A.tocsc()).solve(b)
+    assert rel(x.cpu().numpy(), xs) <= 1e-9
+
+
+def test_mixed_precision_reaches_direct_solution(torus, disk):
+    for c in (torus, disk):
+        b = synth.uniform_rhs(c.n, nrhs=2, seed=8)
+        c.h.set_options(rtol=1e-10, precision=smg.MIXED)
+        x, info = c.h.solve(to_dev(b))
+        c.h.set_options(rtol=1e-10, precision=smg.FP64)
+        assert info["return"] == 0
+        xs = spla.splu(c.A.tocsc()).solve(b)
+        xg = x.cpu().numpy()
+        assert rel(xg, xs) <= 1e-9
+        assert oracle.rel_residual(c.A, xg, b) <= 1e-10
+        ref = oracle.solve_mixed(c.levels, b, opt=oracle.Options(rtol=1e-10))
+        assert abs(info["cycles"] - ref.cycles) <= 1
+
+
+def test_user_matrix_and_t_updates(ico):
+    c = ico
+    b = synth.uniform_rhs(c.n, seed=2)
+    c.h.update_matrix(to_dev(c.levels[0].A.data))
+    x1, i1 = c.h.solve(to_dev(b))
+    c.h.update_positions(c.Vd, c.t)
+    x2, i2 = c.h.solve(to_dev(b))
+    assert i1["cycles"] == i2["cycles"]
+    assert rel(x1.cpu().numpy(), x2.cpu().numpy()) <= CYCLE_TOL
+    c.h.update_t(10 * c.t)
+    A10 = oracle.system_matrix(c.V, c.F, 10 * c.t)
+    got = c.h.level_matrix(0)
+    assert np.abs(got - A10.data).max() <= 1e-14 * np.abs(A10.data).max()
+    c.h.update_t(c.t)
+
+
+def test_warm_start_converged_runs_no_cycle(torus):
+    c = torus
+    b = synth.uniform_rhs(c.n, seed=4)
+    xs = spla.splu(c.A.tocsc()).solve(b)
+    c.h.set_options(rtol=1e-8)
+    _, info = c.h.solve(to_dev(b), to_dev(xs.copy()))
+    c.h.set_options(rtol=1e-10)
+    assert info["cycles"] == 0 and info["return"] == 0
+
+
+def test_single_level_is_direct_solve():
+    V, F = synth.perturbed_icosphere(2, seed=1)
+    c = Case(V, F, 1e-2, max_levels=1)
+    assert c.plan.num_levels == 1
+    b = synth.uniform_rhs(c.n, seed=3)
+    x, info = c.h.solve(to_dev(b))
+    assert info["cycles"] == 1
+    assert oracle.rel_residual(c.A, x.cpu().numpy(), b) <= 1e-13
+
+
+def test_mass_matches_oracle(disk):
+    m = disk.h.mass().cpu().numpy()
+    ref = oracle.lumped_mass(disk.V, disk.F)[disk.u]
+    assert np.abs(m - ref).max() <= 1e-15 * ref.max()
+    x = synth.uniform_rhs(disk.n, nrhs=3, seed=1)
+    y = disk.h.apply_mass(to_dev(x)).cpu().numpy()
+    assert np.abs(y - ref[:, None] * x).max() <= 1e-15 * np.abs(y).max()
+
+
+def test_error_statuses(ico):
+    V, F = synth.perturbed_icosphere(2, seed=1)
+    plan = smg.Plan(V, F, max_levels=2, min_coarse=0)
+    h = smg.Hierarchy(plan)
+    b = to_dev(np.ones(plan.level_info(0)[0]))
+    with pytest.raises(smg.SmgError) as e:
+        h.solve(b)
+    assert e.value.status == 10                       # solve before any update
+    h.update_positions(to_dev(V), 1e-2)
+    with pytest.raises(smg.SmgError) as e:
+        h.solve(to_dev(np.ones((b.shape[0], 5))))
+    assert e.value.status == 1                        # nrhs out of range
+    A = oracle.system_matrix(V, F, 1e-2)
+    h.update_matrix(to_dev(-A.data))                  # negative definite: coarsest pivot fails
+    with pytest.raises(smg.SmgError) as e:
+        h.solve(b)
+    assert e.value.status == 4
+    h.update_matrix(to_dev(A.data))
+    h.set_options(rtol=1e-30, max_cycles=2)
+    _, info = h.solve(b, check=False)
+    assert info["return"] == 5 and info["cycles"] == 2
+    h.close()
