@@ -1,0 +1,460 @@
+#!/usr/bin/env python3
+"""Benchmark of the surface multigrid hot path on GB300.
+
+Workload (1M vertices): torus from a 2000 x 500 grid (R = 1, r = 0.3, 2% normal
+noise), A = M + 1e-3 L, one right-hand side uniform in [-1, 1], paper-default
+hierarchy (ratio 0.25, coarsest >= 500 vertices), V(2,2) multicolour
+Gauss-Seidel, stop at relative residual 1e-9.
+
+A step is one pass of the whole hot path on resident inputs: update (assembly
+of A from the positions, the Galerkin hierarchy, the coarsest Cholesky) and a
+solve from x = 0 to the tolerance.  value = V-cycles per second over the timed
+steps (time per step = time to 1e-9 including the update).  L2 is flushed by a
+256 MB write before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own replica of the workload (the
+path of one mesh does not shard); the value adds all ranks' cycles over the
+slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = dict(name="torus-2000x500-1M", nu=2000, nv=500, R=1.0, r=0.3, noise=0.02, mesh_seed=0,
+                t=1e-3, rtol=1e-9, rhs_seed=1, nrhs=1)
+SMALL = dict(name="torus-400x100-40k", nu=400, nv=100, R=1.0, r=0.3, noise=0.02, mesh_seed=0,
+             t=1e-3, rtol=1e-9, rhs_seed=1, nrhs=1)
+METRIC = "V-cycles/s at 1M verts (solve to rel. residual 1e-9, update included)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_workload(w):
+    V, F = synth.torus(w["nu"], w["nv"], R=w["R"], r=w["r"], noise=w["noise"], seed=w["mesh_seed"])
+    b = synth.uniform_rhs(V.shape[0], nrhs=w["nrhs"], seed=w["rhs_seed"])
+    return V, F, b
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes (CSR figures: values + int32 column indices, row pointers)
+def cycle_bytes(levels, s=8, k=1, mu=4):
+    """Bytes one V(2,2) cycle must move: for every level l < H with n rows and z
+    entries, A_l = z (s + 4) + 4 (n + 1); (mu_pre + mu_post) sweeps of A_l + 3 s k n,
+    the residual and restriction A_l + 2 s k n + 3 (s + 4) n + s k n_c, the
+    prolongation and correction 3 (s + 4) n + s k n_c + 2 s k n; the coarsest
+    solve reads the two triangular inverse factors, n_H^2 binary64 values."""
+    total = 0.0
+    for l in range(len(levels) - 1):
+        n, z = levels[l]
+        nc = levels[l + 1][0]
+        A = z * (s + 4) + 4 * (n + 1)
+        total += mu * (A + 3 * s * k * n)
+        total += A + 2 * s * k * n + 3 * (s + 4) * n + s * k * nc
+        total += 3 * (s + 4) * n + s * k * nc + 2 * s * k * n
+    nH = levels[-1][0]
+    total += nH * nH * 8
+    return total
+
+
+def sweep_bytes(n, z, s=8, k=1):
+    return z * (s + 4) + 4 * (n + 1) + 3 * s * k * n
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (200 ms period)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_levels(V, F, t, plan, timings=None):
+    """Oracle operators on the library's hierarchy; records update timings."""
+    import oracle
+    t0 = time.perf_counter()
+    A = oracle.system_matrix(V, F, t)
+    t1 = time.perf_counter()
+    Ps = [plan.prolongation_csr(l) for l in range(1, plan.num_levels)]
+    mats = [A]
+    for P in Ps:
+        mats.append(oracle.galerkin(mats[-1], P))
+    t2 = time.perf_counter()
+    L = oracle.cholesky(mats[-1].toarray())
+    t3 = time.perf_counter()
+    levels = []
+    for l, P in enumerate(Ps):
+        col = oracle.greedy_colouring(mats[l])
+        levels.append(oracle.Level(A=mats[l], P=P, colour=col, fwd=oracle.colour_order(col),
+                                   rev=oracle.colour_order(col, reverse=True)))
+    levels.append(oracle.Level(A=mats[-1], L=L))
+    if timings is not None:
+        timings.update(assembly_s=t1 - t0, galerkin_s=t2 - t1, cholesky_s=t3 - t2, update_s=t3 - t0)
+    return levels
+
+
+def oracle_cycle_rate(V, F, b, w, plan, cycles_per_solve, sample_cycles):
+    """Oracle V-cycles/s with the same definition as the GPU value."""
+    import oracle
+    tm = {}
+    levels = oracle_levels(V, F, w["t"], plan, tm)
+    x = np.zeros_like(b)
+    t0 = time.perf_counter()
+    for _ in range(sample_cycles):
+        x = oracle.vcycle(levels, 0, np.ascontiguousarray(x), b, oracle.Options())
+    tc = (time.perf_counter() - t0) / sample_cycles
+    per_solve = tm["update_s"] + cycles_per_solve * tc
+    return cycles_per_solve / per_solve, tm, tc
+
+
+# ---------------------------------------------------------------------------
+def kernels_per_cycle(plan, mu=4):
+    nl = plan.num_levels
+    k = 0
+    for l in range(nl - 1):
+        k += mu * plan.level_info(l)[2] + 3          # sweeps + residual + restrict + prolong
+    return k + 2                                       # coarsest: two triangular products
+
+
+def kernels_per_update(plan):
+    nl = plan.num_levels
+    nH = plan.level_info(nl - 1)[0]
+    nb = (nH + 31) // 32
+    fac = 1 + sum(1 + (2 if nb - j - 1 > 0 else 0) for j in range(nb)) + sum(
+        1 + (1 if i + 1 < nb else 0) for i in range(nb)) + 1
+    return 4 + 2 * (nl - 1) + fac
+
+
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    import paper_2104_13755_gb300 as smg
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    V, F, b = make_workload(w)
+    t0 = time.perf_counter()
+    plan = smg.Plan(V, F)
+    setup_s = time.perf_counter() - t0
+    h = smg.Hierarchy(plan, rtol=w["rtol"], max_cycles=200)
+    stream = torch.cuda.current_stream()
+    Vd = torch.from_numpy(V).to(dev)
+    bd = torch.from_numpy(np.ascontiguousarray(b)).to(dev)
+    xd = torch.zeros_like(bd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    levels = [(plan.level_info(l)[0], plan.level_info(l)[1]) for l in range(plan.num_levels)]
+
+    def step(precision=smg.FP64):
+        xd.zero_()
+        h.update_positions(Vd, w["t"])
+        h.solve_async(bd, xd)
+
+    def timed_steps(k, precision):
+        h.set_options(rtol=w["rtol"], max_cycles=200, precision=precision)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        cycles = []
+        for i in range(k):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            step(precision)
+            ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            info = h.solve_result()
+            if info["return"] != 0:
+                raise RuntimeError("solve failed: %s" % info)
+            cycles.append(info["cycles"])
+        return [a.elapsed_time(e) for a, e in ev], cycles
+
+    # warm-up (graph instantiation happens here)
+    for p in (smg.FP64, smg.MIXED):
+        h.set_options(rtol=w["rtol"], max_cycles=200, precision=p)
+        for _ in range(args.warmup):
+            step(p)
+            torch.cuda.synchronize()
+            h.solve_result()
+
+    if args.profile:  # one binary64 and one mixed step inside an NVTX range, then stop
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("smg_profile")
+        for p in (smg.FP64, smg.MIXED):
+            h.set_options(rtol=w["rtol"], max_cycles=200, precision=p)
+            step(p)
+            torch.cuda.synchronize()
+            h.solve_result()
+            # the solve graph's WHILE node hides its kernels from kernel profilers;
+            # one plain cycle graph of each precision exposes them
+            h.run_stage("cycle", precision=p)
+            torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        h.close()
+        return None
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, cycles = timed_steps(args.steps, smg.FP64)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    total_s = sum(ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+    cycles_total = sum(cycles) * world
+    value = cycles_total / total_s
+
+    # mixed precision form, same steps
+    ms_mx, cyc_mx = timed_steps(args.steps, smg.MIXED)
+    h.set_options(rtol=w["rtol"], max_cycles=200, precision=smg.FP64)
+
+    # stage timings with CUDA events on this stream (L2 flushed before each)
+    def stage_ms(stage, reps=10, count=1, **kw):
+        out = []
+        for i in range(reps):
+            flush.fill_(i)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.run_stage(stage, count=count, **kw)
+            e.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(e) / count)
+        return statistics.median(out)
+
+    n0, z0 = levels[0]
+    sweep_ms = stage_ms("sweep", level=0)
+    cyc64_ms = stage_ms("cycle", reps=5, count=5)
+    cyc32_ms = stage_ms("cycle", reps=5, count=5, precision=smg.MIXED)
+    upd_ms = stage_ms("update", reps=5)
+    fac_ms = stage_ms("factor", reps=5)
+    gal_ms = stage_ms("galerkin", level=0, reps=5)
+    # warm per-level sweep cost (10 back-to-back forward sweeps, no flush):
+    # per colour launch = time / (10 * colours)
+    per_level = []
+    for l in range(plan.num_levels - 1):
+        ncol = plan.level_info(l)[2]
+        row = {"level": l, "rows": levels[l][0], "colours": ncol}
+        for name, p in (("f64", smg.FP64), ("f32", smg.MIXED)):
+            h.run_stage("sweep", level=l, precision=p, count=2)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.run_stage("sweep", level=l, precision=p, count=10)
+            e.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(e) / 10
+            row["sweep_us_" + name] = t * 1e3
+            row["per_colour_us_" + name] = t * 1e3 / max(ncol, 1)
+        per_level.append(row)
+    peak, peak_kind = load_peaks()
+    sb = sweep_bytes(n0, z0)
+    achieved = sb / (sweep_ms * 1e-3) / 1e9
+    cb64 = cycle_bytes(levels, s=8)
+    cb32 = cycle_bytes(levels, s=4)
+
+    # end to end through the public API: pinned host inputs in, result out, every step
+    Vh = torch.from_numpy(V).pin_memory()
+    bh = torch.from_numpy(np.ascontiguousarray(b)).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    e2e_ms, e2e_cyc = [], []
+    for i in range(args.steps):
+        flush.fill_(i)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Vd.copy_(Vh, non_blocking=True)
+        bd.copy_(bh, non_blocking=True)
+        xd.zero_()
+        h.update_positions(Vd, w["t"])
+        h.solve_async(bd, xd)
+        xh.copy_(xd, non_blocking=True)
+        e.record(stream)
+        torch.cuda.synchronize()
+        e2e_cyc.append(h.solve_result()["cycles"])
+        e2e_ms.append(a.elapsed_time(e))
+    e2e_value = sum(e2e_cyc) / (sum(e2e_ms) / 1e3) * world
+
+    res = {
+        "metric": METRIC, "value": value, "unit": "V-cycles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "n_vertices": int(V.shape[0]), "faces": int(F.shape[0]),
+                   "levels": [l[0] for l in levels], "nnz": [l[1] for l in levels],
+                   "colours": [plan.level_info(l)[2] for l in range(plan.num_levels)],
+                   "lanes_per_row_f64": [h.level_config(l)[0] for l in range(plan.num_levels - 1)],
+                   "lanes_per_row_f32": [h.level_config(l)[1] for l in range(plan.num_levels - 1)],
+                   "t": w["t"], "rtol": w["rtol"], "nrhs": w["nrhs"], "cycle": "V(2,2) multicolour GS",
+                   "l2": "flushed by a 256 MB write before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_tol_ms": sum(ms) / len(ms),
+        "cycles_per_solve": cycles[0],
+        "setup_s": setup_s,
+        "stages_ms": {"update": upd_ms, "galerkin_l0": gal_ms, "coarsest_factor": fac_ms,
+                      "vcycle_fp64": cyc64_ms, "vcycle_mixed": cyc32_ms, "sweep_l0_fp64": sweep_ms},
+        "per_level_sweeps": per_level,
+        "mixed": {"value": sum(cyc_mx) * world / (sum(ms_mx) / 1e3), "ms_per_step": sum(ms_mx) / len(ms_mx),
+                  "refinement_steps_per_solve": cyc_mx[0]},
+        "roofline": {"kernel": "gs_colour<double,1> level-0 sweep (all colour launches)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "bytes_per_sweep": sb},
+        "roofline_vcycle": {"fp64": {"bytes": cb64, "achieved": cb64 / (cyc64_ms * 1e-3) / 1e9,
+                                     "frac": cb64 / (cyc64_ms * 1e-3) / 1e9 / peak},
+                            "mixed_inner": {"bytes": cb32, "achieved": cb32 / (cyc32_ms * 1e-3) / 1e9,
+                                            "frac": cb32 / (cyc32_ms * 1e-3) / 1e9 / peak}},
+        "e2e": {"value": e2e_value, "unit": "V-cycles/s", "h2d_bytes_per_step": int(Vh.numel() * 8 + bh.numel() * 8),
+                "d2h_bytes_per_step": int(xh.numel() * 8)},
+        "clocks": clocks,
+        "gpu_launches": int(args.steps * (kernels_per_update(plan) + 5) +
+                            sum(cycles) * (kernels_per_cycle(plan) + 2)),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, tm, tc = oracle_cycle_rate(V, F, b, w, plan, cycles[0], sample_cycles=2)
+        res["cpu_baseline"] = {"value": rate, "unit": "V-cycles/s", "cores": 1, "kind": "oracle",
+                               "sample": "oracle update of the full workload (assembly %.1fs, Galerkin %.1fs, "
+                                         "Cholesky %.1fs) + 2 V-cycles (%.2fs each), extrapolated to %d cycles"
+                                         % (tm["assembly_s"], tm["galerkin_s"], tm["cholesky_s"], tc, cycles[0])}
+    h.close()
+    return res
+
+
+def run_reference(args, w, rank, world):
+    """The oracle as it stands, on the host cores, same metric and workload."""
+    if rank != 0:
+        return None
+    import paper_2104_13755_gb300 as smg
+    import oracle
+    V, F, b = make_workload(w)
+    plan = smg.Plan(V, F)
+    tm = {}
+    levels = oracle_levels(V, F, w["t"], plan, tm)
+    ref = oracle.solve(levels, b, opt=oracle.Options(rtol=w["rtol"], max_cycles=200))
+    C = ref.cycles
+    x = np.zeros_like(b)
+    for _ in range(args.warmup):
+        x = oracle.vcycle(levels, 0, np.ascontiguousarray(x), b, oracle.Options())
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x = oracle.vcycle(levels, 0, np.ascontiguousarray(x), b, oracle.Options())
+        times.append(time.perf_counter() - t0)
+    tc = statistics.mean(times)
+    per_solve = tm["update_s"] + C * tc
+    value = C / per_solve
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "V-cycles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3 / C,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "n_vertices": int(V.shape[0]), "t": w["t"], "rtol": w["rtol"],
+                       "parallelism": "host, 1 thread"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "V-cycles/s",
+                             "sample": "each step one oracle V-cycle of the full workload; the oracle update "
+                                       "(%.1f s) is measured once and amortised over the %d cycles of its own "
+                                       "solve to 1e-9" % (tm["update_s"], C)},
+            "e2e": {"value": value, "unit": "V-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--small", action="store_true", help="40k-vertex torus (profiling captures)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="run one step of each precision inside the NVTX range smg_profile and exit")
+    ap.add_argument("--lanes", default=None,
+                    help="lanes per matrix row per level, e.g. 1,2,4,8,8 (skips the autotuner; for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    w = SMALL if args.small else WORKLOAD
+    if args.lanes:
+        os.environ["SMG_LANES_PER_ROW"] = args.lanes
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, w, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        res = run_ours(args, w, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -61,6 +61,9 @@ typedef void *smg_stream;   /* a cudaStream_t */
  *   rtol         stop when max over right-hand sides of ||b - A x|| / ||b|| <= rtol
  *   post_reverse 1: post-relaxation visits the colour classes in reverse order
  *                (symmetric cycle); 0: same order as pre-relaxation
+ *   autotune     1: smg_create times the smoother kernels of every level with
+ *                1, 2, 4, 8 and 16 lanes per matrix row and keeps the fastest
+ *                (binary64 and binary32 separately); 0: a fixed rule
  */
 typedef struct smg_options {
     int32_t mu_pre;
@@ -73,6 +76,7 @@ typedef struct smg_options {
     double  rtol;
     int32_t precision;     /* SMG_FP64 or SMG_MIXED */
     int32_t post_reverse;
+    int32_t autotune;
 } smg_options;
 
 /* Result of one solve (host struct filled by smg_solve). */
@@ -239,6 +243,10 @@ int  smg_level_matrix(smg_hierarchy *h, int level, double *vals_host, smg_stream
 #define SMG_STAGE_UPDATE   5
 int  smg_run_stage(smg_hierarchy *h, int stage, int level, int nrhs, int precision, int count,
                    smg_stream stream);
+
+/* Kernel configuration of level l: out[0] lanes per row of the binary64
+ * kernels, out[1] of the binary32 kernels, out[2] colour classes, out[3] slices. */
+int  smg_level_config(const smg_hierarchy *h, int level, int32_t out[4]);
 
 /* Device bytes held by the hierarchy. */
 int64_t smg_device_bytes(const smg_hierarchy *h);

@@ -30,7 +30,7 @@ class Options(ctypes.Structure):
                 ("min_coarse", ctypes.c_int64), ("max_coarse", ctypes.c_int64),
                 ("max_levels", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("post_reverse", ctypes.c_int32)]
+                ("post_reverse", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -85,6 +85,7 @@ def _load():
         "smg_apply_mass": (I32, [P, P, P, I32, P]),
         "smg_level_matrix": (I32, [P, I32, P, P]),
         "smg_run_stage": (I32, [P, I32, I32, I32, I32, I32, P]),
+        "smg_level_config": (I32, [P, I32, P]),
         "smg_device_bytes": (I64, [P]),
     }
     for name, (res, args) in sig.items():
@@ -341,6 +342,12 @@ class Hierarchy:
         """Enqueue `count` repetitions of one stage (measurement hook, asynchronous)."""
         _check(lib.smg_run_stage(self._h, self.STAGES[stage], level, nrhs, precision, count, _stream_ptr(stream)),
                "smg_run_stage")
+
+    def level_config(self, level):
+        """(lanes per row binary64, lanes per row binary32, colours, slices) of a level."""
+        out = (ctypes.c_int32 * 4)()
+        _check(lib.smg_level_config(self._h, level, out), "smg_level_config")
+        return tuple(out)
 
     @property
     def device_bytes(self):

@@ -36,7 +36,7 @@ def build(force=False, verbose=False):
     jobs, objs = [], []
     for src in host:
         obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
-        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wextra",
+        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-pthread", "-ffp-contract=off", "-Wall", "-Wextra",
                "-I", INC, "-I", "/usr/local/cuda/include", "-c", src, "-o", obj]
         jobs.append((cmd, src))
         objs.append(obj)
@@ -60,7 +60,7 @@ def build(force=False, verbose=False):
         msg = "\n".join("%s:\n%s" % f for f in failed)
         raise RuntimeError("libsmg build failed\n" + msg)
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.run([NVCC, "-shared", ARCH, "-o", tmp] + objs, check=True)
+    subprocess.run([NVCC, "-shared", ARCH, "-o", tmp] + objs + ["-lpthread"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -15,7 +15,7 @@ using namespace smg;
 namespace {
 // ---------------------------------------------------------------- save / load
 const char kMagic[8] = {'S', 'M', 'G', 'P', 'L', 'A', 'N', '1'};
-const int32_t kVersion = 1;
+const int32_t kVersion = 2;
 
 template <class T>
 bool wvec(FILE* f, const std::vector<T>& v) {
@@ -46,6 +46,7 @@ void smg_default_options(smg_options* o) {
     o->rtol = 1e-10;
     o->precision = SMG_FP64;
     o->post_reverse = 1;
+    o->autotune = 1;
 }
 
 const char* smg_status_string(int s) {

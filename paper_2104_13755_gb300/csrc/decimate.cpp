@@ -23,7 +23,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <queue>
 
 #include "smg_host.hpp"
 
@@ -31,7 +30,7 @@ namespace smg {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr double kMinAngle = 1.0 * kPi / 180.0;
+constexpr double kTanMinAngle = 0.017455064928217585;  // tan(1 degree)
 
 struct V3 {
     double x, y, z;
@@ -44,13 +43,55 @@ inline double v3norm(V3 a) { return std::sqrt(v3dot(a, a)); }
 struct HeapItem {
     double len2;
     int32_t a, b;
-    uint32_t va, vb;
 };
-struct HeapCmp {
-    bool operator()(const HeapItem& x, const HeapItem& y) const {
-        if (x.len2 != y.len2) return x.len2 > y.len2;
-        if (x.a != y.a) return x.a > y.a;
-        return x.b > y.b;
+inline bool heap_less(const HeapItem& x, const HeapItem& y) {
+    if (x.len2 != y.len2) return x.len2 < y.len2;
+    if (x.a != y.a) return x.a < y.a;
+    return x.b < y.b;
+}
+
+// 4-ary min-heap: shallower than a binary heap, so fewer cache misses per pop.
+class EdgeHeap {
+   public:
+    void assign(std::vector<HeapItem>&& v) {
+        h_ = std::move(v);
+        for (int64_t i = ((int64_t)h_.size() - 2) / 4; i >= 0; i--) down(i);
+    }
+    bool empty() const { return h_.empty(); }
+    const HeapItem& top() const { return h_[0]; }
+    void push(const HeapItem& x) {
+        h_.push_back(x);
+        int64_t i = (int64_t)h_.size() - 1;
+        while (i > 0) {
+            int64_t p = (i - 1) / 4;
+            if (!heap_less(h_[i], h_[p])) break;
+            std::swap(h_[i], h_[p]);
+            i = p;
+        }
+    }
+    void pop() {
+        h_[0] = h_.back();
+        h_.pop_back();
+        if (!h_.empty()) down(0);
+    }
+
+   private:
+    std::vector<HeapItem> h_;
+    void down(int64_t i) {
+        const int64_t n = (int64_t)h_.size();
+        HeapItem x = h_[i];
+        for (;;) {
+            int64_t c = 4 * i + 1;
+            if (c >= n) break;
+            int64_t best = c;
+            int64_t e = std::min(c + 4, n);
+            for (int64_t k = c + 1; k < e; k++)
+                if (heap_less(h_[k], h_[best])) best = k;
+            if (!heap_less(h_[best], x)) break;
+            h_[i] = h_[best];
+            i = best;
+        }
+        h_[i] = x;
     }
 };
 
@@ -58,7 +99,9 @@ struct HeapCmp {
 struct Flattening {
     int nv = 0;
     std::vector<double> N;    // (2nv)^2 normal matrix
-    double energy_scale = 0;  // sum of areas, used for a relative energy
+    double energy_scale = 0;  // sum of areas
+    mutable std::vector<char> isfix;
+    mutable std::vector<int> freeidx;
     void reset(int nvars) {
         nv = nvars;
         N.assign((size_t)4 * nv * nv, 0.0);
@@ -107,13 +150,13 @@ struct Flattening {
     bool solve(const std::vector<int>& fixed, const std::vector<double>& fixval, std::vector<double>& u,
                std::vector<double>& work) const {
         int d = 2 * nv;
-        std::vector<char> isfix(d, 0);
+        isfix.assign(d, 0);
         u.assign(d, 0.0);
         for (size_t k = 0; k < fixed.size(); k++) {
             isfix[fixed[k]] = 1;
             u[fixed[k]] = fixval[k];
         }
-        std::vector<int> freeidx;
+        freeidx.clear();
         for (int q = 0; q < d; q++)
             if (!isfix[q]) freeidx.push_back(q);
         int f = (int)freeidx.size();
@@ -175,13 +218,12 @@ class Decimator {
     std::vector<double> pos_;
     std::vector<int32_t> fv_;
     std::vector<char> valive_, falive_, vbnd_;
-    std::vector<uint32_t> ver_;
     std::vector<std::vector<int32_t>> vf_;
     // ---- tracked points (one per fine vertex)
     std::vector<int32_t> pface_;  // -1: still exactly at its own vertex
     std::vector<double> pbary_;
     std::vector<std::vector<int32_t>> fpts_;
-    std::priority_queue<HeapItem, std::vector<HeapItem>, HeapCmp> heap_;
+    EdgeHeap heap_;
     DecimationStats* st_ = nullptr;
 
     // ---- per-collapse scratch
@@ -189,6 +231,12 @@ class Decimator {
     std::vector<int> var_of_;  // vertex -> variable (before roles), -1 if not in patch
     Flattening flat_;
     std::vector<double> u_, best_u_, work_;
+    std::vector<int32_t> nb_, occ_, opp_, ni_, nj_, common_, moving_;
+    std::vector<int> fixed_;
+    std::vector<double> fixval_, angsum_, before_sum_, muv_;
+    std::vector<std::pair<int32_t, int>> bv_;
+    // rejected edges, listed at both endpoints; re-queued when a neighbourhood changes
+    std::vector<std::vector<int32_t>> rej_;
 
     V3 P(int32_t v) const { return {pos_[3 * v], pos_[3 * v + 1], pos_[3 * v + 2]}; }
     void push_edge(int32_t a, int32_t b);
@@ -206,7 +254,6 @@ Decimator::Decimator(const MeshData& fine) {
     valive_.assign(n_, 1);
     falive_.assign(m_, 1);
     vbnd_.assign(n_, 0);
-    ver_.assign(n_, 0);
     vf_.assign(n_, {});
     for (int64_t f = 0; f < m_; f++)
         for (int c = 0; c < 3; c++) vf_[fv_[3 * f + c]].push_back((int32_t)f);
@@ -232,12 +279,13 @@ Decimator::Decimator(const MeshData& fine) {
     fpts_.assign(m_, {});
     alive_count_ = n_;
     var_of_.assign(n_, -1);
+    rej_.assign(n_, {});
 }
 
 void Decimator::push_edge(int32_t a, int32_t b) {
     if (a > b) std::swap(a, b);
     V3 d = v3sub(P(a), P(b));
-    heap_.push({v3dot(d, d), a, b, ver_[a], ver_[b]});
+    heap_.push({v3dot(d, d), a, b});
 }
 
 void Decimator::neighbours(int32_t v, std::vector<int32_t>& out) const {
@@ -252,13 +300,13 @@ void Decimator::neighbours(int32_t v, std::vector<int32_t>& out) const {
 }
 
 void Decimator::push_vertex_edges(int32_t v) {
-    std::vector<int32_t> nb;
-    neighbours(v, nb);
-    for (int32_t w : nb) push_edge(v, w);
+    neighbours(v, nb_);
+    for (int32_t w : nb_) push_edge(v, w);
 }
 
 bool Decimator::boundary_neighbours(int32_t v, int32_t nb[2]) const {
-    std::vector<int32_t> occ;
+    std::vector<int32_t>& occ = const_cast<Decimator*>(this)->occ_;
+    occ.clear();
     for (int32_t f : vf_[v])
         for (int c = 0; c < 3; c++) {
             int32_t w = fv_[3 * f + c];
@@ -294,7 +342,8 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
         return false;
     }
     const bool edge_bnd = S_.size() == 1;
-    std::vector<int32_t> opp;
+    std::vector<int32_t>& opp = opp_;
+    opp.clear();
     for (int32_t f : S_)
         for (int c = 0; c < 3; c++) {
             int32_t w = fv_[3 * f + c];
@@ -302,7 +351,8 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
         }
     std::sort(opp.begin(), opp.end());
     {   // link condition: common neighbours of i and j are exactly the opposite vertices
-        std::vector<int32_t> ni, nj, common;
+        std::vector<int32_t>&ni = ni_, &nj = nj_, &common = common_;
+        common.clear();
         neighbours(i, ni);
         neighbours(j, nj);
         std::set_intersection(ni.begin(), ni.end(), nj.begin(), nj.end(), std::back_inserter(common));
@@ -358,11 +408,9 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
         if (std::find(S_.begin(), S_.end(), f) == S_.end()) Fa_.push_back(f);
 
     // cases: 0 interior; 1 boundary vertex i; 2 boundary vertex j; 3,4,5 boundary edge (k=i, k=j, k on ij)
-    std::vector<int> cases;
-    if (edge_bnd) cases = {3, 4, 5};
-    else if (bi) cases = {1};
-    else if (bj) cases = {2};
-    else cases = {0};
+    int cases[3], ncases = 1;
+    if (edge_bnd) { cases[0] = 3; cases[1] = 4; cases[2] = 5; ncases = 3; }
+    else cases[0] = bi ? 1 : (bj ? 2 : 0);
 
     // 3D quality of the new triangles (independent of the flattening)
     for (int32_t f : Fa_) {
@@ -379,9 +427,10 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
             return false;
         }
         for (int c = 0; c < 3; c++) {
+            // angle < 1 degree  <=>  cos > 0 and |sin| < tan(1 deg) cos
             V3 e1 = v3sub(q[(c + 1) % 3], q[c]), e2 = v3sub(q[(c + 2) % 3], q[c]);
-            double ang = std::atan2(v3norm(v3cross(e1, e2)), v3dot(e1, e2));
-            if (!(ang >= kMinAngle)) {
+            double dt = v3dot(e1, e2);
+            if (dt > 0 && !(v3norm(v3cross(e1, e2)) >= kTanMinAngle * dt)) {
                 for (int32_t r : ring_) var_of_[r] = -1;
                 st.rejected_quality++;
                 return false;
@@ -393,7 +442,8 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
     int best_case = -1;
     int best_vi = -1, best_vj = -1, best_vk = -1, best_nv = 0;
     int last_reason = 0;  // 1 solve, 2 flip, 3 angle
-    for (int cs : cases) {
+    for (int ci_ = 0; ci_ < ncases; ci_++) {
+        const int cs = cases[ci_];
         // variable ids: ring 0..nr-1, then i, j, k as the case shares them
         int vi = nr, vj = nr + 1, vk = nr + 2, nv = nr + 3;
         if (cs == 1 || cs == 3) { vk = vi; vj = nr + 1; nv = nr + 2; }
@@ -413,11 +463,14 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
             ok &= flat_.add_triangle(qa, qb, qc, var_after(a), var_after(b), var_after(c));
         }
         if (!ok) { last_reason = 1; continue; }
-        std::vector<int> fixed;
-        std::vector<double> fixval;
+        std::vector<int>& fixed = fixed_;
+        std::vector<double>& fixval = fixval_;
+        fixed.clear();
+        fixval.clear();
         if (cs <= 2) {
             // gauge: the two patch-boundary vertices farthest apart, at (0,0) and (d,0)
-            std::vector<std::pair<int32_t, int>> bv;
+            std::vector<std::pair<int32_t, int>>& bv = bv_;
+            bv.clear();
             for (int32_t r : ring_) bv.push_back({r, var_of_[r]});
             if (cs == 1) bv.push_back({i, vi});
             if (cs == 2) bv.push_back({j, vj});
@@ -439,22 +492,31 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
             int32_t fs = S_[0];
             int ci = fv_[3 * fs] == i ? 0 : (fv_[3 * fs + 1] == i ? 1 : 2);
             double sg = fv_[3 * fs + (ci + 1) % 3] == j ? 1.0 : -1.0;
-            std::vector<int> line;
-            if (cs == 3) { line = {vi, vj, vq}; fixed = {2 * vi, 2 * vq}; fixval = {0.0, sg * (lij + ljq)}; }
-            if (cs == 4) { line = {vp, vi, vj}; fixed = {2 * vp, 2 * vj}; fixval = {0.0, sg * (lpi + lij)}; }
+            int line[5], nline = 0;
+            if (cs == 3) {
+                line[0] = vi; line[1] = vj; line[2] = vq; nline = 3;
+                fixed = {2 * vi, 2 * vq};
+                fixval = {0.0, sg * (lij + ljq)};
+            }
+            if (cs == 4) {
+                line[0] = vp; line[1] = vi; line[2] = vj; nline = 3;
+                fixed = {2 * vp, 2 * vj};
+                fixval = {0.0, sg * (lpi + lij)};
+            }
             if (cs == 5) {
-                line = {vp, vi, vk, vj, vq};
+                line[0] = vp; line[1] = vi; line[2] = vk; line[3] = vj; line[4] = vq; nline = 5;
                 fixed = {2 * vp, 2 * vq};
                 fixval = {0.0, sg * (lpi + lij + ljq)};
             }
-            for (int t : line) { fixed.push_back(2 * t + 1); fixval.push_back(0.0); }
+            for (int q = 0; q < nline; q++) { fixed.push_back(2 * line[q] + 1); fixval.push_back(0.0); }
         }
         if (!flat_.solve(fixed, fixval, u_, work_)) { last_reason = 1; continue; }
         // ---- validity: positive UV triangles, one turn around interior patch vertices
         double scale = 0;
         for (size_t q = 0; q < fixval.size(); q++) scale = std::max(scale, std::fabs(fixval[q]));
         double amin = 1e-12 * scale * scale;
-        std::vector<double> angsum(nv, 0.0);
+        std::vector<double>& angsum = angsum_;
+        angsum.assign(nv, 0.0);
         double uv_area = 0;
         auto tri_ok = [&](int t0, int t1, int t2) {
             double x0 = u_[2 * t0], y0 = u_[2 * t0 + 1], x1 = u_[2 * t1], y1 = u_[2 * t1 + 1];
@@ -465,6 +527,7 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
             int tt[3] = {t0, t1, t2};
             double xs[3] = {x0, x1, x2}, ys[3] = {y0, y1, y2};
             for (int c = 0; c < 3; c++) {
+                if (tt[c] < nr) continue;  // winding is checked at i, j, k only
                 double ax = xs[(c + 1) % 3] - xs[c], ay = ys[(c + 1) % 3] - ys[c];
                 double bx = xs[(c + 2) % 3] - xs[c], by = ys[(c + 2) % 3] - ys[c];
                 angsum[tt[c]] += std::atan2(cross2(ax, ay, bx, by), ax * bx + ay * by);
@@ -476,7 +539,8 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
             int32_t a = fv_[3 * f], b = fv_[3 * f + 1], c = fv_[3 * f + 2];
             valid &= tri_ok(var_before(a), var_before(b), var_before(c));
         }
-        std::vector<double> before_sum = angsum;
+        std::vector<double>& before_sum = before_sum_;
+        before_sum = angsum;
         std::fill(angsum.begin(), angsum.end(), 0.0);
         for (int32_t f : Fa_) {
             int32_t a = fv_[3 * f], b = fv_[3 * f + 1], c = fv_[3 * f + 2];
@@ -518,8 +582,10 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
     const std::vector<double>& U = best_u_;
     auto var_before = [&](int32_t w) { return w == i ? best_vi : (w == j ? best_vj : var_of_[w]); };
     auto var_after = [&](int32_t w) { return (w == i || w == j) ? best_vk : var_of_[w]; };
-    std::vector<int32_t> moving;
-    std::vector<double> muv;
+    std::vector<int32_t>& moving = moving_;
+    std::vector<double>& muv = muv_;
+    moving.clear();
+    muv.clear();
     for (int32_t f : Fb_) {
         for (int32_t p : fpts_[f]) {
             double x = 0, y = 0;
@@ -598,12 +664,16 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
     }
     for (int32_t r : ring_) var_of_[r] = -1;
 
-    // ---------------- versions and new heap entries
-    ver_[i]++;
-    ver_[j]++;
-    for (int32_t r : ring_) ver_[r]++;
+    // ---------------- new heap entries: only k moved, so only its edges change
+    // length; rejected edges around the patch get another chance
+    rej_[i].clear();
+    rej_[j].clear();
     push_vertex_edges(i);
-    for (int32_t r : ring_) push_vertex_edges(r);
+    for (int32_t r : ring_) {
+        for (int32_t w : rej_[r])
+            if (valive_[w] && w != i) push_edge(r, w);
+        rej_[r].clear();
+    }
     st.collapses++;
     return true;
 }
@@ -611,16 +681,32 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
 int Decimator::run(int64_t target, MeshData& coarse, ProlongationRaw& Pout, DecimationStats& st,
                    std::string& err) {
     st_ = &st;
-    for (int64_t f = 0; f < m_; f++)
-        for (int c = 0; c < 3; c++) {
-            int32_t a = fv_[3 * f + c], b = fv_[3 * f + (c + 1) % 3];
-            if (a < b || vbnd_[a] || vbnd_[b]) push_edge(a, b);
-        }
+    {
+        std::vector<HeapItem> init;
+        init.reserve(3 * m_ / 2 + 16);
+        for (int64_t f = 0; f < m_; f++)
+            for (int c = 0; c < 3; c++) {
+                int32_t a = fv_[3 * f + c], b = fv_[3 * f + (c + 1) % 3];
+                if (a < b || vbnd_[a] || vbnd_[b]) {
+                    int32_t lo = std::min(a, b), hi = std::max(a, b);
+                    V3 d = v3sub(P(lo), P(hi));
+                    init.push_back({v3dot(d, d), lo, hi});
+                }
+            }
+        heap_.assign(std::move(init));
+    }
     while (alive_count_ > target && !heap_.empty()) {
         HeapItem e = heap_.top();
         heap_.pop();
-        if (!valive_[e.a] || !valive_[e.b] || ver_[e.a] != e.va || ver_[e.b] != e.vb) continue;
-        try_collapse(e.a, e.b);
+        if (!valive_[e.a] || !valive_[e.b]) continue;
+        // only a collapse's new vertex moves, so an entry whose length no longer
+        // matches is stale (its current length has its own entry)
+        V3 d = v3sub(P(e.a), P(e.b));
+        if (v3dot(d, d) != e.len2) continue;
+        if (!try_collapse(e.a, e.b)) {
+            rej_[e.a].push_back(e.b);
+            rej_[e.b].push_back(e.a);
+        }
     }
     // ---------------- coarse mesh and P_{l+1}
     std::vector<int32_t> newid(n_, -1);

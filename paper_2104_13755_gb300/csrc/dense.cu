@@ -23,46 +23,85 @@ __global__ void k_pad_copy(const double* __restrict__ A, int64_t n, double* __re
     X[e] = (i == j) ? 1.0 : 0.0;
 }
 
+// 1 / sqrt(d) for d > 0: binary32 estimate of the scaled argument refined by two
+// Newton steps y <- y (3 - m y^2) / 2 in binary64 (quadratic convergence from
+// 24 correct bits), with the exponent split off exactly (frexp / ldexp) so the
+// binary32 estimate never under- or overflows.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    int e;
+    double m = frexp(d, &e);  // d = m 2^e, m in [0.5, 1)
+    if (e & 1) {
+        m *= 2.0;
+        e -= 1;
+    }
+    double y = (double)rsqrtf((float)m);
+    y = y * (1.5 - 0.5 * m * y * y);
+    y = y * (1.5 - 0.5 * m * y * y);
+    return ldexp(y, -e / 2);
+}
+
 // Factor diagonal tile j in shared memory and store its triangular inverse.
-__global__ void __launch_bounds__(NB * NB) k_chol_diag(double* __restrict__ C, int64_t np, int j,
-                                                       double* __restrict__ dblk, int32_t* __restrict__ bad) {
-    __shared__ double a[NB][NB + 1];
-    __shared__ double inv[NB][NB + 1];
-    const int r = threadIdx.x / NB, c = threadIdx.x % NB;
+// The pivots form a dependent binary64 chain, so per pivot: warp 0 computes the
+// reciprocal square root and scales the column; one barrier; all threads apply
+// the rank-1 update; one barrier.  The inverse (forward elimination of L X = I)
+// writes final rows to a separate tile, one barrier per step.
+__global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ C, int64_t np, int j,
+                                                   double* __restrict__ dblk, int32_t* __restrict__ bad) {
+    __shared__ double a[NB][NB + 1];    // trailing part
+    __shared__ double l[NB][NB + 1];    // finished factor
+    __shared__ double x[NB][NB + 1];    // inverse in progress
+    __shared__ double xf[NB][NB + 1];   // finished inverse rows
+    __shared__ double rinv[NB];
+    const int c = threadIdx.x % NB, r0 = threadIdx.x / NB;  // rows r0, r0 + 8, r0 + 16, r0 + 24
     double* T = C + (int64_t)j * NB * np + (int64_t)j * NB;
-    a[r][c] = T[(int64_t)r * np + c];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int r = r0 + 8 * q;
+        a[r][c] = T[(int64_t)r * np + c];
+        l[r][c] = 0.0;
+        x[r][c] = (r == c) ? 1.0 : 0.0;
+        xf[r][c] = 0.0;
+    }
     __syncthreads();
     for (int k = 0; k < NB; k++) {
-        if (r == k && c == k) {
+        if (threadIdx.x < 32) {
             double d = a[k][k];
             if (!(d > 0.0) || !isfinite(d)) {  // not SPD: flag it, keep the arithmetic finite
-                atomicExch(bad, 1);
+                if (threadIdx.x == 0) atomicExch(bad, 1);
                 d = 1.0;
             }
-            a[k][k] = sqrt(d);
-        }
-        __syncthreads();
-        if (c == k && r > k) a[r][k] = a[r][k] / a[k][k];
-        __syncthreads();
-        if (c > k && r >= c) a[r][c] -= a[r][k] * a[c][k];
-        __syncthreads();
-    }
-    T[(int64_t)r * np + c] = (c <= r) ? a[r][c] : 0.0;
-    if (r == 0) {  // column c of the inverse of the lower-triangular tile
-        for (int i = 0; i < NB; i++) {
-            double v;
-            if (i < c) v = 0.0;
-            else if (i == c) v = 1.0 / a[c][c];
-            else {
-                double s = 0.0;
-                for (int k = c; k < i; k++) s += a[i][k] * inv[k][c];
-                v = -s / a[i][i];
+            const double y = rsqrt_newton(d);
+            const int rr = threadIdx.x;
+            if (rr == k) {
+                l[k][k] = d * y;
+                rinv[k] = y;
+            } else if (rr > k) {
+                l[rr][k] = a[rr][k] * y;
             }
-            inv[i][c] = v;
         }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int r = r0 + 8 * q;
+            if (c > k && r >= c) a[r][c] -= l[r][k] * l[c][k];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    dblk[(int64_t)j * NB * NB + r * NB + c] = inv[r][c];
+    for (int k = 0; k < NB; k++) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int r = r0 + 8 * q;
+            if (r == k && c <= k) xf[k][c] = x[k][c] * rinv[k];
+            if (r > k && c <= k) x[r][c] -= l[r][k] * (x[k][c] * rinv[k]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int r = r0 + 8 * q;
+        T[(int64_t)r * np + c] = l[r][c];
+        dblk[(int64_t)j * NB * NB + r * NB + c] = xf[r][c];
+    }
 }
 
 // L_ij = A_ij L_jj^{-T} for the tiles below the diagonal tile j.
@@ -76,9 +115,9 @@ __global__ void __launch_bounds__(NB * NB) k_chol_panel(double* __restrict__ C, 
     a[r][c] = T[(int64_t)r * np + c];
     d[r][c] = dblk[(int64_t)j * NB * NB + r * NB + c];
     __syncthreads();
-    double s = 0.0;
-    for (int k = 0; k <= c; k++) s += a[r][k] * d[c][k];
-    T[(int64_t)r * np + c] = s;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};  // four independent partial sums
+    for (int k = 0; k <= c; k++) s[k & 3] += a[r][k] * d[c][k];
+    T[(int64_t)r * np + c] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 __device__ __forceinline__ void tri_index(int b, int& ii, int& kk) {
@@ -100,10 +139,10 @@ __global__ void __launch_bounds__(NB * NB) k_chol_update(double* __restrict__ C,
     li[r][c] = C[((int64_t)i * NB + r) * np + (int64_t)j * NB + c];
     lk[r][c] = C[((int64_t)k * NB + r) * np + (int64_t)j * NB + c];
     __syncthreads();
-    double s = 0.0;
-#pragma unroll 8
-    for (int q = 0; q < NB; q++) s += li[r][q] * lk[c][q];
-    C[((int64_t)i * NB + r) * np + (int64_t)k * NB + c] -= s;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < NB; q++) s[q & 3] += li[r][q] * lk[c][q];
+    C[((int64_t)i * NB + r) * np + (int64_t)k * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 // Block row i of X = L^{-1}: X_i,jb = L_ii^{-1} B_i,jb for jb <= i (B accumulates I - sum L X).
@@ -117,9 +156,9 @@ __global__ void __launch_bounds__(NB * NB) k_trinv_row(double* __restrict__ X, i
     bs[r][c] = T[(int64_t)r * np + c];
     d[r][c] = dblk[(int64_t)i * NB * NB + r * NB + c];
     __syncthreads();
-    double s = 0.0;
-    for (int q = 0; q <= r; q++) s += d[r][q] * bs[q][c];
-    T[(int64_t)r * np + c] = s;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q <= r; q++) s[q & 3] += d[r][q] * bs[q][c];
+    T[(int64_t)r * np + c] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 // B_k,jb -= L_k,i X_i,jb for k > i, jb <= i.
@@ -133,10 +172,10 @@ __global__ void __launch_bounds__(NB * NB) k_trinv_update(double* __restrict__ X
     l[r][c] = C[((int64_t)k * NB + r) * np + (int64_t)i * NB + c];
     xs[r][c] = X[((int64_t)i * NB + r) * np + (int64_t)jb * NB + c];
     __syncthreads();
-    double s = 0.0;
-#pragma unroll 8
-    for (int q = 0; q < NB; q++) s += l[r][q] * xs[q][c];
-    X[((int64_t)k * NB + r) * np + (int64_t)jb * NB + c] -= s;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < NB; q++) s[q & 3] += l[r][q] * xs[q][c];
+    X[((int64_t)k * NB + r) * np + (int64_t)jb * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 __global__ void k_transpose(const double* __restrict__ X, double* __restrict__ XT, int64_t np) {
@@ -154,6 +193,8 @@ __global__ void k_coarse_lower(const double* __restrict__ X, int64_t np, int n, 
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     double acc[K];
 #pragma unroll
     for (int q = 0; q < K; q++) acc[q] = 0.0;
@@ -180,6 +221,8 @@ __global__ void k_coarse_upper(const double* __restrict__ XT, int64_t np, int n,
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     double acc[K];
 #pragma unroll
     for (int q = 0; q < K; q++) acc[q] = 0.0;
@@ -203,11 +246,15 @@ __global__ void k_coarse_upper(const double* __restrict__ XT, int64_t np, int n,
 template <int K>
 void coarse_solve_k(DLevel& C, const void* in, bool in32, void* out, bool out32, cudaStream_t s) {
     const int n = (int)C.n;
-    const int grid = (n + 7) / 8;
-    if (in32) k_coarse_lower<K, true><<<grid, 256, 0, s>>>(C.linv, C.np, n, in, C.y);
-    else k_coarse_lower<K, false><<<grid, 256, 0, s>>>(C.linv, C.np, n, in, C.y);
-    if (out32) k_coarse_upper<K, true><<<grid, 256, 0, s>>>(C.linvT, C.np, n, C.y, out);
-    else k_coarse_upper<K, false><<<grid, 256, 0, s>>>(C.linvT, C.np, n, C.y, out);
+    const dim3 grid((n + 7) / 8), block(256);
+    const double* linv = C.linv;
+    const double* linvT = C.linvT;
+    const double* y = C.y;
+    const int64_t np = C.np;
+    if (in32) launch_pdl(k_coarse_lower<K, true>, grid, block, s, linv, np, n, in, C.y);
+    else launch_pdl(k_coarse_lower<K, false>, grid, block, s, linv, np, n, in, C.y);
+    if (out32) launch_pdl(k_coarse_upper<K, true>, grid, block, s, linvT, np, n, y, out);
+    else launch_pdl(k_coarse_upper<K, false>, grid, block, s, linvT, np, n, y, out);
 }
 
 }  // namespace
@@ -216,19 +263,22 @@ void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s) {
     DLevel& C = h->L[h->H];
     const int64_t np = C.np;
     const int nb = (int)(np / NB);
+    // Cholesky steps on `s`; block row j of the inverse factor needs only diagonal
+    // tile j and panel j, so the inverse runs on a second stream one step behind
+    cudaStream_t s2 = h->aux;
     k_pad_copy<<<(unsigned)((np * np + 255) / 256), 256, 0, s>>>(C.vals, C.n, C.chol, C.linv, np);
     for (int j = 0; j < nb; j++) {
-        k_chol_diag<<<1, NB * NB, 0, s>>>(C.chol, np, j, C.dblk, &h->state->chol_bad);
+        k_chol_diag<<<1, 256, 0, s>>>(C.chol, np, j, C.dblk, &h->state->chol_bad);
         const int T = nb - j - 1;
-        if (T > 0) {
-            k_chol_panel<<<T, NB * NB, 0, s>>>(C.chol, np, j, C.dblk);
-            k_chol_update<<<T * (T + 1) / 2, NB * NB, 0, s>>>(C.chol, np, j);
-        }
+        if (T > 0) k_chol_panel<<<T, NB * NB, 0, s>>>(C.chol, np, j, C.dblk);
+        cudaEventRecord(h->ev_step[j], s);
+        if (T > 0) k_chol_update<<<T * (T + 1) / 2, NB * NB, 0, s>>>(C.chol, np, j);
+        cudaStreamWaitEvent(s2, h->ev_step[j], 0);
+        k_trinv_row<<<j + 1, NB * NB, 0, s2>>>(C.linv, np, j, C.dblk);
+        if (j + 1 < nb) k_trinv_update<<<(nb - j - 1) * (j + 1), NB * NB, 0, s2>>>(C.linv, C.chol, np, j);
     }
-    for (int i = 0; i < nb; i++) {
-        k_trinv_row<<<i + 1, NB * NB, 0, s>>>(C.linv, np, i, C.dblk);
-        if (i + 1 < nb) k_trinv_update<<<(nb - i - 1) * (i + 1), NB * NB, 0, s>>>(C.linv, C.chol, np, i);
-    }
+    cudaEventRecord(h->ev_join, s2);
+    cudaStreamWaitEvent(s, h->ev_join, 0);
     k_transpose<<<dim3(nb, nb), NB * NB, 0, s>>>(C.linv, C.linvT, np);
 }
 

@@ -1,6 +1,8 @@
 // Device hierarchy: upload, update (assembly + Galerkin + coarsest factor),
 // graph-captured V-cycles and the device half of the C ABI.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <stdexcept>
@@ -65,20 +67,54 @@ LevelView<float> view<float>(DLevel& L) {
     return {L.vals32 + L.sbase, L.vals32, L.dinv32, L.p_w32, L.pt_w32, L.x32, L.b32, L.r32};
 }
 
+// Dispatch on the lanes-per-row of a level (compile-time RR inside CALL).
+#define SMG_R_SWITCH(R, CALL)                                \
+    do {                                                     \
+        switch (R) {                                         \
+            case 1: { constexpr int RR = 1; CALL; } break;   \
+            case 2: { constexpr int RR = 2; CALL; } break;   \
+            case 4: { constexpr int RR = 4; CALL; } break;   \
+            case 8: { constexpr int RR = 8; CALL; } break;   \
+            default: { constexpr int RR = 16; CALL; } break; \
+        }                                                    \
+    } while (0)
+
+template <typename T>
+int lanes(const DLevel& L) {
+    return sizeof(T) == 4 ? L.R32 : L.R;
+}
+
 template <typename T, int K>
 void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse, cudaStream_t s) {
+    const int R = lanes<T>(L);
     for (int cc = 0; cc < L.ncolours; cc++) {
         const int c = reverse ? L.ncolours - 1 - cc : cc;
         const int s0 = L.colour_slice[c], s1 = L.colour_slice[c + 1];
         if (s1 <= s0) continue;
-        kern::gs_colour<T, K><<<blocks_for((int64_t)(s1 - s0) * 32), kern::kThreads, 0, s>>>(L.slices, s0, s1, L.sell_col,
-                                                                                            v.sval, v.dinv, b, x);
+        const dim3 grid(blocks_for((int64_t)(s1 - s0) * 32 * R)), block(kern::kThreads);
+        const SliceMeta* sl = L.slices;
+        const int32_t* col = L.sell_col;
+        SMG_R_SWITCH(R, ck(launch_pdl(kern::gs_colour<T, K, RR>, grid, block, s, sl, s0, s1, col, v.sval, v.dinv,
+                                        b, x), "gs launch"));
     }
 }
 
-// One V-cycle of Alg. 2 on the level buffers (x_0, b_0 of the chosen precision).
 template <typename T, int K>
-void rec_vcycle(smg_hierarchy* h, bool zero_x0, cudaStream_t s) {
+void rec_residual(DLevel& L, const LevelView<T>& v, cudaStream_t s) {
+    const int R = lanes<T>(L);
+    const dim3 grid(blocks_for((int64_t)L.nslices * 32 * R)), block(kern::kThreads);
+    const SliceMeta* sl = L.slices;
+    const int32_t* col = L.sell_col;
+    const T* b = v.b;
+    const T* x = v.x;
+    SMG_R_SWITCH(R, ck(launch_pdl(kern::residual<T, K, RR>, grid, block, s, sl, L.nslices, col, v.sval, v.diag, b,
+                                    x, v.r), "residual launch"));
+}
+
+// One V-cycle of Alg. 2 on the level buffers (x_0, b_0 of the chosen precision).
+// Coarse levels start from x = 0: the restriction kernel writes that zero.
+template <typename T, int K>
+void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
     const int H = h->H;
     const bool single = sizeof(T) == 4;
     for (int l = 0; l < H; l++) {
@@ -86,12 +122,12 @@ void rec_vcycle(smg_hierarchy* h, bool zero_x0, cudaStream_t s) {
         DLevel& N = h->L[l + 1];
         LevelView<T> v = view<T>(L);
         LevelView<T> vn = view<T>(N);
-        if (l > 0 || zero_x0) ck(cudaMemsetAsync(v.x, 0, sizeof(T) * L.n * K, s), "memset");  // coarse levels start from 0
         for (int it = 0; it < h->opts.mu_pre; it++) rec_sweep<T, K>(L, v, v.b, v.x, false, s);  // pre-relaxation
-        kern::residual<T, K><<<blocks_for((int64_t)L.nslices * 32), kern::kThreads, 0, s>>>(
-            L.slices, L.nslices, L.sell_col, v.sval, v.diag, v.b, v.x, v.r);
-        kern::restrict_rows<T, K><<<blocks_for(N.n), kern::kThreads, 0, s>>>((int)N.n, L.pt_ptr, L.pt_row, v.pt_w, v.r,
-                                                                             vn.b);
+        rec_residual<T, K>(L, v, s);
+        const dim3 grid(blocks_for(N.n * 4)), block(kern::kThreads);
+        const T* r = v.r;
+        ck(launch_pdl(kern::restrict_rows<T, K>, grid, block, s, (int)N.n, L.pt_ptr, L.pt_row, v.pt_w, r, vn.b,
+                      vn.x), "restrict launch");
     }
     DLevel& C = h->L[H];
     LevelView<T> vc = view<T>(C);
@@ -101,19 +137,28 @@ void rec_vcycle(smg_hierarchy* h, bool zero_x0, cudaStream_t s) {
         DLevel& N = h->L[l + 1];
         LevelView<T> v = view<T>(L);
         LevelView<T> vn = view<T>(N);
-        kern::prolong_add<T, K><<<blocks_for(L.n), kern::kThreads, 0, s>>>((int)L.n, L.p_idx, v.p_w, vn.x, v.x);
+        const dim3 grid(blocks_for(L.n)), block(kern::kThreads);
+        const T* xc = vn.x;
+        ck(launch_pdl(kern::prolong_add<T, K>, grid, block, s, (int)L.n, (const int32_t*)L.p_idx, v.p_w, xc, v.x),
+           "prolong launch");
         for (int it = 0; it < h->opts.mu_post; it++) rec_sweep<T, K>(L, v, v.b, v.x, h->opts.post_reverse != 0, s);
     }
 }
 
-// Level-0 residual norm partials (binary64), optionally writing the binary32 residual.
+// Level-0 residual norm partials (binary64); with r32 also the binary32 residual
+// (next inner right-hand side) and a zero binary32 iterate.
 template <int K>
 void rec_resnorm(smg_hierarchy* h, bool init, bool r32, cudaStream_t s) {
     DLevel& L = h->L[0];
     float* out32 = L.b32;
+    float* x32 = L.x32;
+    const dim3 grid(kern::kNormBlocks), block(kern::kThreads);
+    const double* b = L.b;
+    const double* x = L.x;
+    const double* vals = L.vals;
     if (L.coarsest) {
         const int n = (int)L.n;
-#define SMG_RN(I, R) kern::resnorm_dense<K, I, R><<<kern::kNormBlocks, kern::kThreads, 0, s>>>(n, L.vals, L.b, L.x, h->partials, out32)
+#define SMG_RN(I, R32) ck(launch_pdl(kern::resnorm_dense<K, I, R32>, grid, block, s, n, vals, b, x, h->partials, out32, x32), "resnorm")
         if (init && r32) SMG_RN(true, true);
         else if (init) SMG_RN(true, false);
         else if (r32) SMG_RN(false, true);
@@ -121,10 +166,12 @@ void rec_resnorm(smg_hierarchy* h, bool init, bool r32, cudaStream_t s) {
 #undef SMG_RN
         return;
     }
-#define SMG_RN(I, R)                                                                                         \
-    kern::resnorm<K, I, R><<<kern::kNormBlocks, kern::kThreads, 0, s>>>(L.slices, L.nslices, L.sell_col, \
-                                                                        L.vals + L.sbase, L.vals, L.b, L.x, \
-                                                                        h->partials, out32)
+    const SliceMeta* sl = L.slices;
+    const int32_t* col = L.sell_col;
+    const double* sval = L.vals + L.sbase;
+#define SMG_RN(I, R32)                                                                                            \
+    SMG_R_SWITCH(L.R, ck(launch_pdl(kern::resnorm<K, RR, I, R32>, grid, block, s, sl, L.nslices, col, sval, vals, b, \
+                                    x, h->partials, out32, x32), "resnorm"))
     if (init && r32) SMG_RN(true, true);
     else if (init) SMG_RN(true, false);
     else if (r32) SMG_RN(false, true);
@@ -138,22 +185,27 @@ void rec_cycle_fp64(smg_hierarchy* h, cudaStream_t s) {
         DLevel& C = h->L[0];
         record_coarsest_solve(h, K, C.b, false, C.x, false, s);
     } else {
-        rec_vcycle<double, K>(h, false, s);
+        rec_vcycle<double, K>(h, s);
     }
 }
 
 template <int K>
 void rec_cycle_mixed(smg_hierarchy* h, cudaStream_t s) {
     DLevel& L0 = h->L[0];
+    // the binary32 iterate x32_0 was zeroed by the residual kernel that wrote b32_0
     if (h->H == 0) record_coarsest_solve(h, K, L0.b32, true, L0.x32, true, s);
-    else rec_vcycle<float, K>(h, true, s);
-    kern::ir_update<<<blocks_for(L0.n * K), kern::kThreads, 0, s>>>(L0.n * K, L0.x32, L0.x);
+    else rec_vcycle<float, K>(h, s);
+    const float* d = L0.x32;
+    ck(launch_pdl(kern::ir_update, dim3(blocks_for(L0.n * K)), dim3(kern::kThreads), s, (int64_t)(L0.n * K), d, L0.x),
+       "ir update");
 }
 
 template <int K>
 void rec_final(smg_hierarchy* h, cudaGraphConditionalHandle hnd, bool init, bool use_cond, cudaStream_t s) {
-    kern::norm_final<K><<<1, kern::kThreads, 0, s>>>(h->partials, kern::kNormBlocks, h->state, hnd, init ? 1 : 0,
-                                                     h->opts.rtol, h->opts.max_cycles, use_cond ? 1 : 0);
+    const double* part = h->partials;
+    ck(launch_pdl(kern::norm_final<K>, dim3(1), dim3(kern::kThreads), s, part, (int)kern::kNormBlocks, h->state, hnd,
+                  init ? 1 : 0, h->opts.rtol, h->opts.max_cycles, use_cond ? 1 : 0),
+       "norm final");
 }
 
 template <int K>
@@ -241,6 +293,80 @@ cudaGraphExec_t cycle_graph(smg_hierarchy* h, int K, bool mixed) {
     return e;
 }
 
+// Lanes per row of the smoother kernels, per level and precision: the fastest
+// of 1, 2, 4, 8, 16 over timed forward sweeps (values are irrelevant to the
+// cost; the buffers hold zeros at this point).  Without tuning, the fewest
+// lanes leaving at most eight entries per lane in the widest slices.
+void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
+    const char* env = std::getenv("SMG_LANES_PER_ROW");
+    cudaEvent_t e0, e1;
+    if (tune) {
+        ck(cudaEventCreate(&e0), "event");
+        ck(cudaEventCreate(&e1), "event");
+    }
+    for (int l = 0; l < h->H; l++) {
+        DLevel& L = h->L[l];
+        const LevelPlan& lp = P.L[l];
+        std::vector<int32_t> w;
+        for (const SliceMeta& s : lp.slices) w.push_back(s.width);
+        std::sort(w.begin(), w.end());
+        const int p90 = w.empty() ? 0 : w[(size_t)(0.9 * (double)(w.size() - 1))];
+        int R = 1;
+        while (R < 16 && (p90 + R - 1) / R > 8) R *= 2;
+        L.R = L.R32 = R;
+        if (env) {  // "R" for every level, or "R0,R1,..." per level
+            std::string spec(env);
+            size_t pos = 0;
+            int r = 0;
+            for (int q = 0; q <= l && pos != std::string::npos; q++) {
+                r = std::atoi(spec.c_str() + pos);
+                size_t comma = spec.find(',', pos);
+                if (q < l) pos = comma == std::string::npos ? std::string::npos : comma + 1;
+            }
+            if (r == 1 || r == 2 || r == 4 || r == 8 || r == 16) L.R = L.R32 = r;
+            continue;
+        }
+        if (!tune) continue;
+        for (int prec = 0; prec < 2; prec++) {
+            float best = 1e30f;
+            int bestR = R;
+            for (int cand : {1, 2, 4, 8, 16}) {
+                if (prec == 0) L.R = cand;
+                else L.R32 = cand;
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; rep++) {
+                    if (prec == 0) {
+                        LevelView<double> v = view<double>(L);
+                        rec_sweep<double, 1>(L, v, v.b, v.x, false, h->cap);
+                        ck(cudaEventRecord(e0, h->cap), "event");
+                        for (int it = 0; it < 4; it++) rec_sweep<double, 1>(L, v, v.b, v.x, false, h->cap);
+                    } else {
+                        LevelView<float> v = view<float>(L);
+                        rec_sweep<float, 1>(L, v, v.b, v.x, false, h->cap);
+                        ck(cudaEventRecord(e0, h->cap), "event");
+                        for (int it = 0; it < 4; it++) rec_sweep<float, 1>(L, v, v.b, v.x, false, h->cap);
+                    }
+                    ck(cudaEventRecord(e1, h->cap), "event");
+                    ck(cudaEventSynchronize(e1), "event sync");
+                    float t = 0.f;
+                    ck(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+                    ms = rep == 0 ? t : std::min(ms, t);
+                }
+                if (ms < best * 0.97f) {  // a larger R must win clearly
+                    best = ms;
+                    bestR = cand;
+                }
+            }
+            if (prec == 0) L.R = bestR;
+            else L.R32 = bestR;
+        }
+    }
+    if (tune) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+}
+
 // Galerkin chain, level preparation and the coarsest factor, as one graph.
 void build_update_graph(smg_hierarchy* h) {
     cudaStream_t s = h->cap;
@@ -276,7 +402,11 @@ void free_all(smg_hierarchy* h) {
     if (h->update_exec) cudaGraphExecDestroy(h->update_exec);
     for (void* p : h->allocs) cudaFree(p);
     if (h->state_host) cudaFreeHost(h->state_host);
+    for (auto e : h->ev_step)
+        if (e) cudaEventDestroy(e);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->aux) cudaStreamDestroy(h->aux);
     h->allocs.clear();
 }
 
@@ -285,6 +415,7 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
     h->opts = o;
     h->H = (int)P.L.size() - 1;
     ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    ck(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking), "cudaStreamCreate");
     h->L.resize(P.L.size());
     for (int l = 0; l <= h->H; l++) {
         const LevelPlan& lp = P.L[l];
@@ -295,6 +426,7 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
         L.nflat = lp.nflat;
         L.nslots = lp.nslots;
         L.ncolours = lp.ncolours;
+        L.R = 1;
         L.nslices = (int)lp.slices.size();
         L.colour_slice = lp.colour_slice;
         L.flat_to_csr = lp.flat_to_csr;
@@ -313,6 +445,9 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
             L.linv = dalloc<double>(h, L.np * L.np);
             L.linvT = dalloc<double>(h, L.np * L.np);
             L.dblk = dalloc<double>(h, L.np * kDenseNB);
+            h->ev_step.assign(L.np / kDenseNB, nullptr);
+            for (auto& e : h->ev_step) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+            ck(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event");
             L.y = dalloc<double>(h, L.n * kMaxRhs);
             continue;
         }
@@ -353,6 +488,8 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
     ck(cudaMemset(h->state, 0, sizeof(SolveState)), "memset");
     h->partials = dalloc<double>(h, (int64_t)kern::kNormBlocks * 2 * kMaxRhs);
     ck(cudaMallocHost((void**)&h->state_host, sizeof(SolveState)), "cudaMallocHost");
+    ck(cudaDeviceSynchronize(), "upload");
+    choose_lanes(h, P, o.autotune != 0);
     build_update_graph(h);
     ck(cudaDeviceSynchronize(), "setup");
 }
@@ -387,6 +524,7 @@ int smg_create(const smg_plan* plan, const smg_options* opts, smg_hierarchy** ou
         o.rtol = opts->rtol;
         o.precision = opts->precision;
         o.post_reverse = opts->post_reverse;
+        o.autotune = opts->autotune;
     }
     if (o.mu_pre < 0 || o.mu_post < 0 || o.max_cycles < 0 || !(o.rtol >= 0))
         return fail("invalid solve options", SMG_ERR_INVALID_ARG);
@@ -633,8 +771,7 @@ int smg_run_stage(smg_hierarchy* h, int stage, int level, int nrhs, int precisio
                 break;
             case SMG_STAGE_RESIDUAL: {
                 LevelView<double> v = view<double>(L);
-                kern::residual<double, 1><<<blocks_for((int64_t)L.nslices * 32), kern::kThreads, 0, s>>>(
-                    L.slices, L.nslices, L.sell_col, v.sval, v.diag, v.b, v.x, v.r);
+                rec_residual<double, 1>(L, v, s);
                 break;
             }
             case SMG_STAGE_GALERKIN: {
@@ -651,6 +788,16 @@ int smg_run_stage(smg_hierarchy* h, int stage, int level, int nrhs, int precisio
     ck(cudaGetLastError(), "stage launches");
     return SMG_OK;
     SMG_GUARD_END
+}
+
+int smg_level_config(const smg_hierarchy* h, int level, int32_t out[4]) {
+    if (!h || !out || level < 0 || level > h->H) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    const DLevel& L = h->L[level];
+    out[0] = L.R;
+    out[1] = L.R32;
+    out[2] = L.ncolours;
+    out[3] = L.nslices;
+    return SMG_OK;
 }
 
 int64_t smg_device_bytes(const smg_hierarchy* h) { return h ? h->bytes : 0; }

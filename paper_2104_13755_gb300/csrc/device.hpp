@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <map>
+#include <utility>
 #include <vector>
 
 #include "plan.hpp"
@@ -29,6 +30,8 @@ struct DLevel {
     int64_t n = 0, sbase = 0, nflat = 0, nslots = 0;
     bool coarsest = false;
     int ncolours = 0, nslices = 0;
+    int R = 1;    // lanes per row of the binary64 kernels
+    int R32 = 1;  // lanes per row of the binary32 kernels
     std::vector<int32_t> colour_slice;  // host copy, ncolours + 1
     SliceMeta* slices = nullptr;
     int32_t* sell_col = nullptr;
@@ -84,6 +87,9 @@ struct smg_hierarchy {
     smg::SolveState* state_host = nullptr;  // pinned
     double* partials = nullptr;             // [kNormBlocks][2 * kMaxRhs]
     cudaStream_t cap = nullptr;             // private capture stream
+    cudaStream_t aux = nullptr;             // second capture stream (parallel graph branch)
+    std::vector<cudaEvent_t> ev_step;       // fork points of the coarsest factorisation
+    cudaEvent_t ev_join = nullptr;
     cudaGraphExec_t update_exec = nullptr;
     std::map<int, cudaGraphExec_t> solve_exec;   // key precision * 16 + nrhs
     std::map<int, cudaGraphExec_t> cycle_exec;   // key precision * 16 + nrhs
@@ -97,7 +103,27 @@ namespace smg {
 // and its transpose) on `s`; launches only, capturable.
 void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s);
 // dense.cu: x = A_H^{-1} b through the inverse factor; `in`/`out` are binary64 or
-// binary32 vectors (n x K row-major) as the flags say.
+// binary32 vectors (n x K row-major) as the flags say.  Launched as programmatic
+// dependents (they wait for the preceding kernel before reading `in`).
 void record_coarsest_solve(smg_hierarchy* h, int K, const void* in, bool in32, void* out, bool out32,
                            cudaStream_t s);
+// Launch with programmatic stream serialization: under stream capture the edge to
+// the previous kernel becomes a programmatic dependency, so this kernel may start
+// before its predecessor finishes and must call griddepcontrol.wait before
+// reading anything that predecessor (or an earlier kernel) writes.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 }  // namespace smg

@@ -1,11 +1,12 @@
 // Sparse kernels of the V-cycle (Alg. 2) and the per-frame update.
 //
 // Layout (per level, rows permuted colour-major): the off-diagonal entries sit in
-// SELL-32 slices -- 32 consecutive rows of one colour class, entry k of lane r at
-// slot off + 32 k + r -- so every warp-wide load of values or column indices is
-// one contiguous, aligned 128/256-byte segment.  The diagonal is stored apart
-// (and its reciprocal for the Gauss-Seidel update).  Vectors with K right-hand
-// sides are row-major n x K, so a neighbour gather reads K adjacent values.
+// warp-sized slices of one colour class with R lanes per row (R chosen per level
+// so a lane holds few entries; see SliceMeta), so every warp-wide load of values
+// or column indices is one contiguous, aligned 128/256-byte segment and all
+// gathers of a row are in flight together.  The diagonal is stored apart (and
+// its reciprocal for the Gauss-Seidel update).  Vectors with K right-hand sides
+// are row-major n x K, so a neighbour gather reads K adjacent values.
 #pragma once
 
 #include "device.hpp"
@@ -23,88 +24,174 @@ __device__ __forceinline__ T ldg(const T* p) {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Kernels of a cycle are launched so that the
+// next kernel may start while the previous one drains: everything a kernel
+// reads that no kernel of the cycle writes (matrix entries, slice headers,
+// prolongation weights) is loaded before pdl_wait(); everything produced by an
+// earlier kernel is read after it.  pdl_wait() returns once the preceding grid
+// has completed and its writes are visible (immediately when launched
+// without the attribute); pdl_trigger() lets the following grid start.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Entries per lane loaded ahead of the dependency wait.
+template <typename T, int K>
+struct Pre {
+    static constexpr int value = (K <= 2 || sizeof(T) == 4) ? 8 : 4;
+};
+
+// A warp covers 32 / R rows of a SELL-32 slice (sub-slice g of R), R lanes per
+// row: lane = sub * (32 / R) + rl holds entries k = sub, sub + R, ... of row
+// g * (32 / R) + rl, so the lanes of one `sub` read contiguous slots.  acc gets
+// -sum_k a_k x_{c_k}, summed over the R lanes of a row by a fixed xor tree.
+template <typename T, int K, int R, int PRE>
+struct RowSlice {
+    static constexpr int RL = 32 / R;  // rows per warp
+    int c[PRE];
+    T v[PRE];
+    int W, sub, r;
+    __device__ __forceinline__ void load(const SliceMeta& m, int g, int lane, const int32_t* __restrict__ col,
+                                         const T* __restrict__ sval) {
+        W = m.width;
+        sub = lane / RL;
+        r = g * RL + (lane % RL);
+#pragma unroll
+        for (int u = 0; u < PRE; u++) {
+            const int k = sub + R * u;
+            if (k < W) {
+                c[u] = ldg(col + m.off + k * 32 + r);
+                v[u] = ldg(sval + m.off + k * 32 + r);
+            }
+        }
+    }
+    // x may be written by this launch at other rows only, or read-only
+    __device__ __forceinline__ void dot(const SliceMeta& m, const int32_t* __restrict__ col,
+                                        const T* __restrict__ sval, const T* x, T (&acc)[K]) const {
+        T xv[PRE][K];
+#pragma unroll
+        for (int u = 0; u < PRE; u++)
+            if (sub + R * u < W)
+#pragma unroll
+                for (int q = 0; q < K; q++) xv[u][q] = ldg(x + (int64_t)c[u] * K + q);
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] = T(0);
+#pragma unroll
+        for (int u = 0; u < PRE; u++)
+            if (sub + R * u < W)
+#pragma unroll
+                for (int q = 0; q < K; q++) acc[q] -= v[u] * xv[u][q];
+        for (int k = sub + R * PRE; k < W; k += R) {  // rows longer than PRE * R: the rare tail
+            const int cc = ldg(col + m.off + k * 32 + r);
+            const T vv = ldg(sval + m.off + k * 32 + r);
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[q] -= vv * ldg(x + (int64_t)cc * K + q);
+        }
+#pragma unroll
+        for (int o = 16; o >= RL; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Multicolour Gauss-Seidel (App. "Multi-Color Gauss Seidel"): one colour class,
 // x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii for every row i of the class.
 // No row of a class is coupled to another row of the same class, so the rows
-// update in parallel and the x values read here are not written by this launch.
-template <typename T, int K>
+// update in parallel and the x values gathered here are not written by this
+// launch (padding entries point at the row itself with value 0).
+template <typename T, int K, int R>
 __global__ void __launch_bounds__(kThreads) gs_colour(const SliceMeta* __restrict__ slices, int s0, int s1,
                                                       const int32_t* __restrict__ col, const T* __restrict__ sval,
                                                       const T* __restrict__ dinv, const T* __restrict__ b,
                                                       T* __restrict__ x) {
-    const int s = s0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int s = s0 + w / R;
     const int lane = threadIdx.x & 31;
     if (s >= s1) return;
     const SliceMeta m = slices[s];
-    const int row = m.row0 + lane;
-    const bool valid = lane < m.nrows;
+    RowSlice<T, K, R, Pre<T, K>::value> rs;
+    rs.load(m, w % R, lane, col, sval);
+    const bool valid = rs.r < m.nrows;
+    const int row = m.row0 + (valid ? rs.r : 0);
+    const T d = dinv[row];
+    pdl_wait();
+    pdl_trigger();
     T acc[K];
+    rs.dot(m, col, sval, x, acc);
+    if (valid && rs.sub == 0)
 #pragma unroll
-    for (int q = 0; q < K; q++) acc[q] = valid ? b[(int64_t)row * K + q] : T(0);
-    const int32_t* cp = col + m.off + lane;
-    const T* vp = sval + m.off + lane;
-#pragma unroll 4
-    for (int k = 0; k < m.width; k++) {
-        const int c = ldg(cp + k * 32);
-        const T v = ldg(vp + k * 32);
-#pragma unroll
-        for (int q = 0; q < K; q++) acc[q] -= v * ldg(x + (int64_t)c * K + q);
-    }
-    if (valid) {
-        const T d = dinv[row];
-#pragma unroll
-        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = acc[q] * d;
-    }
+        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = (b[(int64_t)row * K + q] + acc[q]) * d;
 }
 
 // r = b - A x over all rows of a level.
-template <typename T, int K>
+template <typename T, int K, int R>
 __global__ void __launch_bounds__(kThreads) residual(const SliceMeta* __restrict__ slices, int nslices,
                                                      const int32_t* __restrict__ col, const T* __restrict__ sval,
                                                      const T* __restrict__ diag, const T* __restrict__ b,
                                                      const T* __restrict__ x, T* __restrict__ r) {
-    const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int s = w / R;
     const int lane = threadIdx.x & 31;
     if (s >= nslices) return;
     const SliceMeta m = slices[s];
-    const int row = m.row0 + lane;
-    if (lane >= m.nrows) return;
-    T acc[K];
+    RowSlice<T, K, R, Pre<T, K>::value> rs;
+    rs.load(m, w % R, lane, col, sval);
+    const bool valid = rs.r < m.nrows;
+    const int row = m.row0 + (valid ? rs.r : 0);
     const T d = diag[row];
+    pdl_wait();
+    pdl_trigger();
+    T acc[K];
+    rs.dot(m, col, sval, x, acc);
+    if (valid && rs.sub == 0)
 #pragma unroll
-    for (int q = 0; q < K; q++) acc[q] = b[(int64_t)row * K + q] - d * x[(int64_t)row * K + q];
-    const int32_t* cp = col + m.off + lane;
-    const T* vp = sval + m.off + lane;
-#pragma unroll 4
-    for (int k = 0; k < m.width; k++) {
-        const int c = ldg(cp + k * 32);
-        const T v = ldg(vp + k * 32);
-#pragma unroll
-        for (int q = 0; q < K; q++) acc[q] -= v * ldg(x + (int64_t)c * K + q);
-    }
-#pragma unroll
-    for (int q = 0; q < K; q++) r[(int64_t)row * K + q] = acc[q];
+        for (int q = 0; q < K; q++)
+            r[(int64_t)row * K + q] = (b[(int64_t)row * K + q] - d * x[(int64_t)row * K + q]) + acc[q];
 }
 
-// Restriction r_{h+1} = P^T r_h (Alg. 2 "restrict residual"), one coarse row per
-// thread through the CSR of P^T: a deterministic gather.
+// Restriction r_{h+1} = P^T r_h (Alg. 2 "restrict residual") through the CSR of
+// P^T, four lanes per coarse row, plus the zero start x_{h+1} = 0 of the coarse
+// cycle (the coarse iterate is not read again before its pre-relaxation).
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) restrict_rows(int nc, const int32_t* __restrict__ ptr,
                                                           const int32_t* __restrict__ rows, const T* __restrict__ w,
-                                                          const T* __restrict__ r, T* __restrict__ bc) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
+                                                          const T* __restrict__ r, T* __restrict__ bc,
+                                                          T* __restrict__ xc) {
+    constexpr int RR = 4, PREP = 4;
+    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) / RR);
+    const int sub = threadIdx.x % RR;
+    const int I = g < nc ? g : nc - 1;
+    const int k0 = ptr[I], k1 = ptr[I + 1];
+    int ri[PREP];
+    T wi[PREP];
+#pragma unroll
+    for (int u = 0; u < PREP; u++) {
+        const int k = k0 + sub + u * RR;
+        ri[u] = k < k1 ? rows[k] : 0;
+        wi[u] = k < k1 ? w[k] : T(0);
+    }
+    pdl_wait();
+    pdl_trigger();
     T acc[K];
 #pragma unroll
     for (int q = 0; q < K; q++) acc[q] = T(0);
-    for (int k = ptr[I]; k < ptr[I + 1]; k++) {
-        const int i = rows[k];
-        const T wk = w[k];
 #pragma unroll
-        for (int q = 0; q < K; q++) acc[q] += wk * ldg(r + (int64_t)i * K + q);
-    }
+    for (int u = 0; u < PREP; u++)
 #pragma unroll
-    for (int q = 0; q < K; q++) bc[(int64_t)I * K + q] = acc[q];
+        for (int q = 0; q < K; q++) acc[q] += wi[u] * ldg(r + (int64_t)ri[u] * K + q);
+    for (int k = k0 + sub + PREP * RR; k < k1; k += RR)
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] += w[k] * ldg(r + (int64_t)rows[k] * K + q);
+#pragma unroll
+    for (int o = RR / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (g < nc && sub == 0)
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            bc[(int64_t)I * K + q] = acc[q];
+            xc[(int64_t)I * K + q] = T(0);
+        }
 }
 
 // Prolongation with the correction add, x_h <- x_h + P c (Alg. 2 "prolong
@@ -115,60 +202,66 @@ __global__ void __launch_bounds__(kThreads) prolong_add(int n, const int32_t* __
                                                         T* __restrict__ x) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    T acc[K];
-#pragma unroll
-    for (int q = 0; q < K; q++) acc[q] = T(0);
+    int c[3];
+    T wa[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        const int c = idx[(int64_t)a * n + p];
-        const T wa = w[(int64_t)a * n + p];
-#pragma unroll
-        for (int q = 0; q < K; q++) acc[q] += wa * ldg(xc + (int64_t)c * K + q);
+        c[a] = idx[(int64_t)a * n + p];
+        wa[a] = w[(int64_t)a * n + p];
     }
+    pdl_wait();
+    pdl_trigger();
+    T xv[3][K];
 #pragma unroll
-    for (int q = 0; q < K; q++) x[(int64_t)p * K + q] += acc[q];
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int q = 0; q < K; q++) xv[a][q] = ldg(xc + (int64_t)c[a] * K + q);
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        T acc = wa[0] * xv[0][q] + wa[1] * xv[1][q] + wa[2] * xv[2][q];
+        x[(int64_t)p * K + q] += acc;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Level-0 residual norms for the stopping test of Alg. 1, reduced in a fixed
 // order (fixed grid, fixed tree) so the result is bitwise reproducible.
 // INIT also accumulates ||b||^2; R32 also stores the residual in binary32 (the
-// right-hand side of the next inner cycle of the mixed-precision form).
-template <int K, bool INIT, bool R32>
+// right-hand side of the next inner cycle of the mixed-precision form) and
+// zeroes that cycle's binary32 iterate.
+template <int K, int R, bool INIT, bool R32>
 __global__ void __launch_bounds__(kThreads) resnorm(const SliceMeta* __restrict__ slices, int nslices,
                                                     const int32_t* __restrict__ col, const double* __restrict__ sval,
                                                     const double* __restrict__ diag, const double* __restrict__ b,
                                                     const double* __restrict__ x, double* __restrict__ partials,
-                                                    float* __restrict__ r32) {
+                                                    float* __restrict__ r32, float* __restrict__ x32) {
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
+    pdl_wait();
+    pdl_trigger();
     double rr[K], bb[K];
 #pragma unroll
     for (int q = 0; q < K; q++) rr[q] = bb[q] = 0.0;
-    for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < nslices; s += gridDim.x * kWarps) {
-        const SliceMeta m = slices[s];
-        const int row = m.row0 + lane;
-        if (lane >= m.nrows) continue;
+    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nslices * R; w += gridDim.x * kWarps) {
+        const SliceMeta m = slices[w / R];
+        RowSlice<double, K, R, Pre<double, K>::value> rs;
+        rs.load(m, w % R, lane, col, sval);
         double acc[K];
-        const double d = diag[row];
+        rs.dot(m, col, sval, x, acc);
+        if (rs.r < m.nrows && rs.sub == 0) {
+            const int row = m.row0 + rs.r;
+            const double d = diag[row];
 #pragma unroll
-        for (int q = 0; q < K; q++) {
-            const double bv = b[(int64_t)row * K + q];
-            acc[q] = bv - d * x[(int64_t)row * K + q];
-            if (INIT) bb[q] += bv * bv;
-        }
-        const int32_t* cp = col + m.off + lane;
-        const double* vp = sval + m.off + lane;
-        for (int k = 0; k < m.width; k++) {
-            const int c = ldg(cp + k * 32);
-            const double v = ldg(vp + k * 32);
-#pragma unroll
-            for (int q = 0; q < K; q++) acc[q] -= v * ldg(x + (int64_t)c * K + q);
-        }
-#pragma unroll
-        for (int q = 0; q < K; q++) {
-            rr[q] += acc[q] * acc[q];
-            if (R32) r32[(int64_t)row * K + q] = (float)acc[q];
+            for (int q = 0; q < K; q++) {
+                const double bv = b[(int64_t)row * K + q];
+                const double rv = (bv - d * x[(int64_t)row * K + q]) + acc[q];
+                rr[q] += rv * rv;
+                if (INIT) bb[q] += bv * bv;
+                if (R32) {
+                    r32[(int64_t)row * K + q] = (float)rv;
+                    x32[(int64_t)row * K + q] = 0.0f;
+                }
+            }
         }
     }
     __shared__ double red[kWarps][2 * K];
@@ -197,9 +290,12 @@ __global__ void __launch_bounds__(kThreads) resnorm(const SliceMeta* __restrict_
 template <int K, bool INIT, bool R32>
 __global__ void __launch_bounds__(kThreads) resnorm_dense(int n, const double* __restrict__ A,
                                                           const double* __restrict__ b, const double* __restrict__ x,
-                                                          double* __restrict__ partials, float* __restrict__ r32) {
+                                                          double* __restrict__ partials, float* __restrict__ r32,
+                                                          float* __restrict__ x32) {
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
+    pdl_wait();
+    pdl_trigger();
     double rr[K], bb[K];
 #pragma unroll
     for (int q = 0; q < K; q++) rr[q] = bb[q] = 0.0;
@@ -220,7 +316,10 @@ __global__ void __launch_bounds__(kThreads) resnorm_dense(int n, const double* _
             if (lane == 0) {
                 rr[q] += rv * rv;
                 if (INIT) bb[q] += bv * bv;
-                if (R32) r32[(int64_t)i * K + q] = (float)rv;
+                if (R32) {
+                    r32[(int64_t)i * K + q] = (float)rv;
+                    x32[(int64_t)i * K + q] = 0.0f;
+                }
             }
         }
     }
@@ -246,6 +345,8 @@ template <int K>
 __global__ void norm_final(const double* __restrict__ partials, int nblocks, SolveState* __restrict__ st,
                            cudaGraphConditionalHandle hnd, int init, double rtol, int max_cycles, int use_cond) {
     __shared__ double red[kThreads][2 * K];
+    pdl_wait();
+    pdl_trigger();
     double acc[2 * K];
 #pragma unroll
     for (int q = 0; q < 2 * K; q++) acc[q] = 0.0;
@@ -425,6 +526,8 @@ __global__ void scatter_rows(int64_t n, int K, const int32_t* __restrict__ perm,
 __global__ void ir_update(int64_t m, const float* __restrict__ d, double* __restrict__ x) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m) return;
+    pdl_wait();
+    pdl_trigger();
     x[e] += (double)d[e];
 }
 

@@ -1,13 +1,44 @@
 // Geometry-only setup: level loop, Dirichlet reduction, symbolic Galerkin
 // patterns, Alg. 3 colourings and the device-ready layouts.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <thread>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
 #include "plan.hpp"
 
 namespace smg {
+
+// Run body(begin, end) over [0, n) in contiguous chunks on up to 16 host threads.
+template <class Body>
+static void parallel_rows(int64_t n, Body body) {
+    int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+    if (n < 4096) nt = 1;
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; t++) {
+        int64_t a = n * t / nt, b = n * (t + 1) / nt;
+        if (t + 1 == nt) body(a, b);
+        else th.emplace_back(body, a, b);
+    }
+    for (auto& x : th) x.join();
+}
+
+// Setup trace: with SMG_TRACE_SETUP set, every stage prints its wall time to stderr.
+struct StageTimer {
+    bool on = std::getenv("SMG_TRACE_SETUP") != nullptr;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void mark(const char* what) {
+        if (!on) return;
+        auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "[smg setup] %-28s %8.3f s\n", what, std::chrono::duration<double>(now - t).count());
+        t = now;
+    }
+};
 
 static int validate_mesh(const double* V, int64_t n, const int32_t* F, int64_t m, std::string& err) {
     if (!V || !F || n < 3 || m < 1 || n > (int64_t)INT32_MAX / 4 || m > (int64_t)INT32_MAX / 4) {
@@ -78,7 +109,9 @@ int build_plan(const double* V, int64_t n, const int32_t* F, int64_t m, const ui
         MeshData next;
         ProlongationRaw P;
         DecimationStats ds;
+        StageTimer dt;
         if (decimate_level(cur, target, next, P, ds, err) != 0) return SMG_ERR_DECIMATION;
+        dt.mark("decimation level");
         if (next.n() >= nc) break;
         p.meshes.push_back(std::move(next));
         p.praw.push_back(std::move(P));
@@ -134,26 +167,8 @@ static int64_t csr_find(const std::vector<int64_t>& rp, const std::vector<int32_
     return (int64_t)(it - ci.begin());
 }
 
-// slot of (I, J), I != J, in the SELL layout of level `lv` (permuted indices), -1 if absent
-static int64_t sell_find(const LevelPlan& lv, const std::vector<int32_t>& slice_of_row, int32_t I, int32_t J) {
-    const SliceMeta& s = lv.slices[slice_of_row[I]];
-    int lane = I - s.row0;
-    int lo = 0, hi = s.width;
-    while (lo < hi) {  // columns of a row ascend; padding (the row itself) sorts last
-        int mid = (lo + hi) / 2;
-        int32_t c = lv.sell_col[(size_t)s.off + (size_t)mid * kSlice + lane];
-        bool pad = (c == I);
-        if (!pad && c < J) lo = mid + 1;
-        else hi = mid;
-    }
-    if (lo < s.width) {
-        int32_t c = lv.sell_col[(size_t)s.off + (size_t)lo * kSlice + lane];
-        if (c == J && c != I) return (int64_t)s.off + (int64_t)lo * kSlice + lane;
-    }
-    return -1;
-}
-
 int finalize_plan(Plan& p, std::string& err) {
+    StageTimer tm;
     const int H = (int)p.meshes.size() - 1;
     const MeshData& m0 = p.meshes[0];
     const int64_t n0 = m0.n();
@@ -230,6 +245,7 @@ int finalize_plan(Plan& p, std::string& err) {
             }
     }
 
+    tm.mark("dirichlet + reduced P");
     // ---- symbolic patterns
     {
         LevelPlan& lv = p.L[0];
@@ -261,6 +277,7 @@ int finalize_plan(Plan& p, std::string& err) {
         return SMG_ERR_DECIMATION;
     }
 
+    tm.mark("symbolic Galerkin patterns");
     // ---- colouring, permutation and SELL-32 layout per level
     for (int l = 0; l <= H; l++) {
         LevelPlan& lv = p.L[l];
@@ -287,6 +304,7 @@ int finalize_plan(Plan& p, std::string& err) {
             return len[a] > len[b];
         });
         for (int64_t q = 0; q < n; q++) lv.iperm[lv.perm[q]] = (int32_t)q;
+        const int rows_per_slice = kSlice;
         lv.colour_row.assign(lv.ncolours + 1, 0);
         for (int64_t r = 0; r < n; r++) lv.colour_row[lv.colour[r] + 1]++;
         for (int c = 0; c < lv.ncolours; c++) lv.colour_row[c + 1] += lv.colour_row[c];
@@ -294,10 +312,10 @@ int finalize_plan(Plan& p, std::string& err) {
         lv.colour_slice.assign(lv.ncolours + 1, 0);
         int64_t off = 0;
         for (int c = 0; c < lv.ncolours; c++) {
-            for (int32_t r0 = lv.colour_row[c]; r0 < lv.colour_row[c + 1]; r0 += kSlice) {
+            for (int32_t r0 = lv.colour_row[c]; r0 < lv.colour_row[c + 1]; r0 += rows_per_slice) {
                 SliceMeta s;
                 s.row0 = r0;
-                s.nrows = std::min(kSlice, lv.colour_row[c + 1] - r0);
+                s.nrows = std::min(rows_per_slice, lv.colour_row[c + 1] - r0);
                 s.width = 0;
                 for (int k = 0; k < s.nrows; k++) s.width = std::max(s.width, len[lv.perm[r0 + k]]);
                 if (off > (int64_t)INT32_MAX - (int64_t)s.width * kSlice) {
@@ -316,20 +334,20 @@ int finalize_plan(Plan& p, std::string& err) {
         lv.sell_col.assign(off, 0);
         std::vector<int32_t> cols;
         for (const SliceMeta& s : lv.slices)
-            for (int lane = 0; lane < kSlice; lane++) {
-                int32_t prow = s.row0 + (lane < s.nrows ? lane : 0);
+            for (int rl = 0; rl < rows_per_slice; rl++) {
+                int32_t prow = s.row0 + (rl < s.nrows ? rl : 0);
                 cols.clear();
-                if (lane < s.nrows) {
+                if (rl < s.nrows) {
                     int32_t r = lv.perm[prow];
                     for (int64_t q = lv.rowptr[r]; q < lv.rowptr[r + 1]; q++)
                         if (lv.col[q] != r) cols.push_back(lv.iperm[lv.col[q]]);
                     std::sort(cols.begin(), cols.end());
                 }
-                for (int k = 0; k < s.width; k++)
-                    lv.sell_col[(size_t)s.off + (size_t)k * kSlice + lane] = k < (int)cols.size() ? cols[k] : prow;
+                for (int k = 0; k < s.width; k++) lv.sell_col[slot_at(s, rl, k)] = k < (int)cols.size() ? cols[k] : prow;
             }
     }
 
+    tm.mark("colouring + SELL layout");
     // ---- flat index -> natural CSR position
     for (int l = 0; l <= H; l++) {
         LevelPlan& lv = p.L[l];
@@ -341,10 +359,10 @@ int finalize_plan(Plan& p, std::string& err) {
         }
         for (int64_t pr = 0; pr < lv.n; pr++) lv.flat_to_csr[pr] = csr_find(lv.rowptr, lv.col, lv.perm[pr], lv.perm[pr]);
         for (const SliceMeta& s : lv.slices)
-            for (int lane = 0; lane < s.nrows; lane++) {
-                int32_t pr = s.row0 + lane;
+            for (int rl = 0; rl < s.nrows; rl++) {
+                int32_t pr = s.row0 + rl;
                 for (int k = 0; k < s.width; k++) {
-                    int64_t slot = (int64_t)s.off + (int64_t)k * kSlice + lane;
+                    int64_t slot = slot_at(s, rl, k);
                     int32_t pc = lv.sell_col[slot];
                     if (pc == pr) continue;
                     lv.flat_to_csr[lv.sbase + slot] = csr_find(lv.rowptr, lv.col, lv.perm[pr], lv.perm[pc]);
@@ -352,6 +370,7 @@ int finalize_plan(Plan& p, std::string& err) {
             }
     }
 
+    tm.mark("flat -> CSR maps");
     // ---- permuted prolongation, restriction and Galerkin plans
     for (int l = 0; l < H; l++) {
         LevelPlan& lv = p.L[l];
@@ -386,24 +405,23 @@ int finalize_plan(Plan& p, std::string& err) {
                         fill[I]++;
                     }
         }
-        // Galerkin contributions: fine entry (p, q) with value a_pq adds
-        // P[p, I] a_pq P[q, J] to coarse (I, J) for every weight pair.
+        // Galerkin contributions, gathered per coarse row I: every fine row p with
+        // P[p, I] != 0 and every entry a_pq of that row adds P[p, I] a_pq P[q, J] to
+        // coarse entry (I, J) for each weight P[q, J] of row q.
         std::vector<int32_t> nx_slice_of_row;
         if (!nx.coarsest) {
             nx_slice_of_row.assign(nc, 0);
-            for (size_t s = 0; s < nx.slices.size(); s++)
-                for (int k = 0; k < nx.slices[s].nrows; k++) nx_slice_of_row[nx.slices[s].row0 + k] = (int32_t)s;
+            for (size_t si = 0; si < nx.slices.size(); si++)
+                for (int k = 0; k < nx.slices[si].nrows; k++) nx_slice_of_row[nx.slices[si].row0 + k] = (int32_t)si;
         }
-        auto dst_of = [&](int32_t I, int32_t J) -> int64_t {
-            if (nx.coarsest) return (int64_t)I * nc + J;
-            if (I == J) return I;
-            int64_t s = sell_find(nx, nx_slice_of_row, I, J);
-            return s < 0 ? -1 : nx.sbase + s;
-        };
+        std::vector<int32_t> fine_slice(n, 0);
+        for (size_t si = 0; si < lv.slices.size(); si++)
+            for (int k = 0; k < lv.slices[si].nrows; k++) fine_slice[lv.slices[si].row0 + k] = (int32_t)si;
+        // two passes (count, fill); coarse rows are split across host threads, and
+        // every destination belongs to exactly one row, so the threads never share one
         lv.g_ptr.assign(nx.nflat + 1, 0);
-        bool bad = false;
+        std::atomic<bool> bad{false};
         for (int pass = 0; pass < 2 && !bad; pass++) {
-            std::vector<int64_t> fill;
             if (pass == 1) {
                 for (int64_t d = 0; d < nx.nflat; d++) lv.g_ptr[d + 1] += lv.g_ptr[d];
                 if (lv.g_ptr[nx.nflat] > (int64_t)INT32_MAX) {
@@ -412,39 +430,63 @@ int finalize_plan(Plan& p, std::string& err) {
                 }
                 lv.g_src.assign(lv.g_ptr[nx.nflat], 0);
                 lv.g_w.assign(lv.g_ptr[nx.nflat], 0.0);
-                fill.assign(lv.g_ptr.begin(), lv.g_ptr.end() - 1);
             }
-            auto emit = [&](int32_t pr, int32_t pc, int64_t e) {
-                for (int a = 0; a < 3; a++) {
-                    double wa = lv.p_w[a * n + pr];
-                    if (wa == 0.0) continue;
-                    int32_t I = lv.p_idx[a * n + pr];
-                    for (int b = 0; b < 3; b++) {
-                        double wb = lv.p_w[b * n + pc];
-                        if (wb == 0.0) continue;
-                        int64_t d = dst_of(I, lv.p_idx[b * n + pc]);
-                        if (d < 0) {
-                            bad = true;
-                            return;
+            parallel_rows(nc, [&](int64_t I0, int64_t I1) {
+                std::vector<int32_t> stamp(nc, -1);
+                std::vector<int64_t> slot_of(nc, -1);
+                for (int64_t I = I0; I < I1 && !bad; I++) {
+                    if (!nx.coarsest) {  // column -> flat slot of coarse row I
+                        const SliceMeta& cs = nx.slices[nx_slice_of_row[I]];
+                        const int rl = (int)(I - cs.row0);
+                        for (int k = 0; k < cs.width; k++) {
+                            int64_t slot = slot_at(cs, rl, k);
+                            int32_t c = nx.sell_col[slot];
+                            if (c == I) continue;
+                            stamp[c] = (int32_t)I;
+                            slot_of[c] = nx.sbase + slot;
                         }
-                        if (pass == 0) lv.g_ptr[d + 1]++;
-                        else {
-                            lv.g_src[fill[d]] = (int32_t)e;
-                            lv.g_w[fill[d]] = wa * wb;
-                            fill[d]++;
+                    }
+                    auto dst_of = [&](int32_t J) -> int64_t {
+                        if (nx.coarsest) return I * nc + J;
+                        if (J == I) return I;
+                        return stamp[J] == I ? slot_of[J] : -1;
+                    };
+                    for (int32_t t = lv.pt_ptr[I]; t < lv.pt_ptr[I + 1]; t++) {
+                        const int32_t pr = lv.pt_row[t];
+                        const double wI = lv.pt_w[t];
+                        auto entry = [&](int32_t pc, int64_t e) {
+                            for (int b = 0; b < 3; b++) {
+                                double wb = lv.p_w[b * n + pc];
+                                if (wb == 0.0) continue;
+                                int64_t d = dst_of(lv.p_idx[b * n + pc]);
+                                if (d < 0) {
+                                    bad = true;
+                                    return;
+                                }
+                                if (pass == 0) lv.g_ptr[d + 1]++;
+                                else {
+                                    int64_t k = lv.g_ptr[d]++;
+                                    lv.g_src[k] = (int32_t)e;
+                                    lv.g_w[k] = wI * wb;
+                                }
+                            }
+                        };
+                        entry(pr, pr);
+                        const SliceMeta& fs = lv.slices[fine_slice[pr]];
+                        const int rl = pr - fs.row0;
+                        for (int k = 0; k < fs.width; k++) {
+                            int64_t slot = slot_at(fs, rl, k);
+                            int32_t pc = lv.sell_col[slot];
+                            if (pc == pr) continue;
+                            entry(pc, lv.sbase + slot);
                         }
                     }
                 }
-            };
-            for (int64_t pr = 0; pr < n; pr++) emit((int32_t)pr, (int32_t)pr, pr);
-            for (const SliceMeta& s : lv.slices)
-                for (int lane = 0; lane < s.nrows; lane++)
-                    for (int k = 0; k < s.width; k++) {
-                        int64_t slot = (int64_t)s.off + (int64_t)k * kSlice + lane;
-                        int32_t pc = lv.sell_col[slot];
-                        if (pc == s.row0 + lane) continue;
-                        emit(s.row0 + lane, pc, lv.sbase + slot);
-                    }
+            });
+            if (pass == 1) {  // the fill advanced every g_ptr[d] to the start of d + 1
+                for (int64_t d = nx.nflat; d > 0; d--) lv.g_ptr[d] = lv.g_ptr[d - 1];
+                lv.g_ptr[0] = 0;
+            }
         }
         if (bad) {
             err = "internal: Galerkin destination missing from the symbolic pattern";
@@ -452,6 +494,7 @@ int finalize_plan(Plan& p, std::string& err) {
         }
     }
 
+    tm.mark("transfer + Galerkin plans");
     // ---- level-0 assembly plan
     AssemblyPlan& A = p.asmb;
     const LevelPlan& l0 = p.L[0];
@@ -502,17 +545,18 @@ int finalize_plan(Plan& p, std::string& err) {
                     if (I != J) opp_of(A.row_vertex[I], A.row_vertex[J], A.opp0[I * l0.n + J], A.opp1[I * l0.n + J]);
         } else {
             for (const SliceMeta& s : l0.slices)
-                for (int lane = 0; lane < s.nrows; lane++)
+                for (int rl = 0; rl < s.nrows; rl++)
                     for (int k = 0; k < s.width; k++) {
-                        int64_t slot = (int64_t)s.off + (int64_t)k * kSlice + lane;
+                        int64_t slot = slot_at(s, rl, k);
                         int32_t pc = l0.sell_col[slot];
-                        if (pc == s.row0 + lane) continue;
-                        opp_of(A.row_vertex[s.row0 + lane], A.row_vertex[pc], A.opp0[l0.sbase + slot],
+                        if (pc == s.row0 + rl) continue;
+                        opp_of(A.row_vertex[s.row0 + rl], A.row_vertex[pc], A.opp0[l0.sbase + slot],
                                A.opp1[l0.sbase + slot]);
                     }
         }
         A.flat_to_user = l0.flat_to_csr;
     }
+    tm.mark("assembly plan");
     return SMG_OK;
 }
 

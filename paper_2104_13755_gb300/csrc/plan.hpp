@@ -12,13 +12,19 @@ namespace smg {
 
 constexpr int kSlice = 32;  // rows per SELL slice (one warp)
 
-// Per-slice header of the SELL-32 off-diagonal storage.
+// Per-slice header of the SELL-32 off-diagonal storage: 32 consecutive rows of
+// one colour class; entry k of the row at local position r sits at slot
+// off + 32 k + r, so a warp-wide load of one entry of 32 rows is one contiguous
+// 128/256-byte segment.  Kernels may split a slice over R warps (R lanes per
+// row, 32 / R rows per warp): each load step then reads R segments.
 struct SliceMeta {
     int32_t row0;   // first (permuted) row of the slice
     int32_t nrows;  // rows in the slice (<= 32; the last slice of a colour may be short)
     int32_t width;  // padded off-diagonal entries per row
-    int32_t off;    // first slot; entry k of lane r sits at off + k * 32 + r
+    int32_t off;    // first slot of the slice
 };
+
+inline int64_t slot_at(const SliceMeta& s, int r, int k) { return (int64_t)s.off + (int64_t)k * kSlice + r; }
 
 struct LevelPlan {
     int64_t n = 0;
