@@ -348,6 +348,8 @@ def run_ours(args, w, rank, world, local_rank):
                    "colours": [plan.level_info(l)[2] for l in range(plan.num_levels)],
                    "lanes_per_row_f64": [h.level_config(l)[0] for l in range(plan.num_levels - 1)],
                    "lanes_per_row_f32": [h.level_config(l)[1] for l in range(plan.num_levels - 1)],
+                   "cluster_tail_from_level": {"f64": h.cycle_config()[1], "f32": h.cycle_config()[2],
+                                               "ctas": h.cycle_config()[3]},
                    "t": w["t"], "rtol": w["rtol"], "nrhs": w["nrhs"], "cycle": "V(2,2) multicolour GS",
                    "l2": "flushed by a 256 MB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -62,8 +62,10 @@ typedef void *smg_stream;   /* a cudaStream_t */
  *   post_reverse 1: post-relaxation visits the colour classes in reverse order
  *                (symmetric cycle); 0: same order as pre-relaxation
  *   autotune     1: smg_create times the smoother kernels of every level with
- *                1, 2, 4, 8 and 16 lanes per matrix row and keeps the fastest
- *                (binary64 and binary32 separately); 0: a fixed rule
+ *                1, 2, 4, 8 and 16 lanes per matrix row and keeps the fastest,
+ *                then times whole cycles to choose the first level of the
+ *                cluster-resident tail (binary64 and binary32 separately);
+ *                0: fixed size rules
  */
 typedef struct smg_options {
     int32_t mu_pre;
@@ -247,6 +249,12 @@ int  smg_run_stage(smg_hierarchy *h, int stage, int level, int nrhs, int precisi
 /* Kernel configuration of level l: out[0] lanes per row of the binary64
  * kernels, out[1] of the binary32 kernels, out[2] colour classes, out[3] slices. */
 int  smg_level_config(const smg_hierarchy *h, int level, int32_t out[4]);
+
+/* Cycle configuration: out[0] = H, out[1] / out[2] = first level whose
+ * smoothing and transfers run inside one thread-block cluster launch per
+ * half-cycle for binary64 / binary32 cycles (H = none), out[3] = CTAs per
+ * cluster (0 when the device offers no cluster launch). */
+int  smg_cycle_config(const smg_hierarchy *h, int32_t out[4]);
 
 /* Device bytes held by the hierarchy. */
 int64_t smg_device_bytes(const smg_hierarchy *h);

@@ -86,6 +86,7 @@ def _load():
         "smg_level_matrix": (I32, [P, I32, P, P]),
         "smg_run_stage": (I32, [P, I32, I32, I32, I32, I32, P]),
         "smg_level_config": (I32, [P, I32, P]),
+        "smg_cycle_config": (I32, [P, P]),
         "smg_device_bytes": (I64, [P]),
     }
     for name, (res, args) in sig.items():
@@ -347,6 +348,12 @@ class Hierarchy:
         """(lanes per row binary64, lanes per row binary32, colours, slices) of a level."""
         out = (ctypes.c_int32 * 4)()
         _check(lib.smg_level_config(self._h, level, out), "smg_level_config")
+        return tuple(out)
+
+    def cycle_config(self):
+        """(H, first cluster-tail level binary64, binary32, CTAs per cluster)."""
+        out = (ctypes.c_int32 * 4)()
+        _check(lib.smg_cycle_config(self._h, out), "smg_cycle_config")
         return tuple(out)
 
     @property

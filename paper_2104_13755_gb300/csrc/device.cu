@@ -2,13 +2,14 @@
 // graph-captured V-cycles and the device half of the C ABI.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 #include <stdexcept>
 #include <string>
 
-#include "kernels.cuh"
+#include "tail.cuh"
 
 using namespace smg;
 
@@ -48,6 +49,8 @@ std::vector<float> to_f32(const std::vector<double>& v) {
     for (size_t k = 0; k < v.size(); k++) o[k] = (float)v[k];
     return o;
 }
+
+void drop_graphs(smg_hierarchy* h);
 
 // ------------------------------------------------------------------ launchers
 template <typename T>
@@ -111,13 +114,27 @@ void rec_residual(DLevel& L, const LevelView<T>& v, cudaStream_t s) {
                                     x, v.r), "residual launch"));
 }
 
+template <typename T, int K>
+void rec_tail(smg_hierarchy* h, bool down, int t, cudaStream_t s) {
+    const bool single = sizeof(T) == 4;
+    const TailLevel<T>* lv = (const TailLevel<T>*)(single ? h->tail_lv32 : h->tail_lv64);
+    const dim3 block(kern::kTailThreads);
+    if (down) ck(launch_cluster_pdl(kern::tail_down<T, K>, h->tail_cluster, block, s, lv, t, h->H, h->opts.mu_pre),
+                 "tail down");
+    else ck(launch_cluster_pdl(kern::tail_up<T, K>, h->tail_cluster, block, s, lv, t, h->H, h->opts.mu_post,
+                               h->opts.post_reverse != 0 ? 1 : 0),
+            "tail up");
+}
+
 // One V-cycle of Alg. 2 on the level buffers (x_0, b_0 of the chosen precision).
 // Coarse levels start from x = 0: the restriction kernel writes that zero.
+// Levels [t, H) run in the cluster tail kernels.
 template <typename T, int K>
 void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
     const int H = h->H;
     const bool single = sizeof(T) == 4;
-    for (int l = 0; l < H; l++) {
+    const int t = std::min(single ? h->tail32 : h->tail64, H);
+    for (int l = 0; l < t; l++) {
         DLevel& L = h->L[l];
         DLevel& N = h->L[l + 1];
         LevelView<T> v = view<T>(L);
@@ -129,10 +146,12 @@ void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
         ck(launch_pdl(kern::restrict_rows<T, K>, grid, block, s, (int)N.n, L.pt_ptr, L.pt_row, v.pt_w, r, vn.b,
                       vn.x), "restrict launch");
     }
+    if (t < H) rec_tail<T, K>(h, true, t, s);
     DLevel& C = h->L[H];
     LevelView<T> vc = view<T>(C);
     record_coarsest_solve(h, K, vc.b, single, vc.x, single, s);  // direct solve at level H
-    for (int l = H - 1; l >= 0; l--) {
+    if (t < H) rec_tail<T, K>(h, false, t, s);
+    for (int l = t - 1; l >= 0; l--) {
         DLevel& L = h->L[l];
         DLevel& N = h->L[l + 1];
         LevelView<T> v = view<T>(L);
@@ -352,6 +371,9 @@ void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
                     ck(cudaEventElapsedTime(&t, e0, e1), "elapsed");
                     ms = rep == 0 ? t : std::min(ms, t);
                 }
+                if (std::getenv("SMG_TRACE_TUNE"))
+                    std::fprintf(stderr, "[smg tune] level %d %s sweep, %2d lanes/row: %.1f us\n", l,
+                                 prec ? "f32" : "f64", cand, ms * 250.0f);
                 if (ms < best * 0.97f) {  // a larger R must win clearly
                     best = ms;
                     bestR = cand;
@@ -365,6 +387,137 @@ void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
+}
+
+template <typename T>
+std::vector<TailLevel<T>> tail_table(smg_hierarchy* h) {
+    std::vector<TailLevel<T>> tab(h->H);
+    for (int l = 0; l < h->H; l++) {
+        DLevel& L = h->L[l];
+        DLevel& N = h->L[l + 1];
+        LevelView<T> v = view<T>(L);
+        LevelView<T> vn = view<T>(N);
+        TailLevel<T>& t = tab[l];
+        t.slices = L.slices;
+        t.col = L.sell_col;
+        t.sval = v.sval;
+        t.dinv = v.dinv;
+        t.diag = v.diag;
+        t.colour_slice = L.colour_slice_dev;
+        t.x = v.x;
+        t.b = v.b;
+        t.r = v.r;
+        t.nslices = L.nslices;
+        t.ncolours = L.ncolours;
+        t.n = (int)L.n;
+        t.pt_ptr = L.pt_ptr;
+        t.pt_row = L.pt_row;
+        t.pt_w = v.pt_w;
+        t.n_next = (int)N.n;
+        t.b_next = vn.b;
+        t.x_next = vn.x;
+        t.p_idx = L.p_idx;
+        t.p_w = v.p_w;
+    }
+    return tab;
+}
+
+template <typename T, int K>
+void allow_wide_clusters() {
+    cudaFuncSetAttribute(kern::tail_down<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(kern::tail_up<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+// CTAs per tail cluster: 16 (non-portable) when the device can schedule it, else
+// the portable 8, else 0 (no tail).
+int detect_tail_cluster() {
+    allow_wide_clusters<double, 1>();
+    allow_wide_clusters<double, 2>();
+    allow_wide_clusters<double, 3>();
+    allow_wide_clusters<double, 4>();
+    allow_wide_clusters<float, 1>();
+    allow_wide_clusters<float, 2>();
+    allow_wide_clusters<float, 3>();
+    allow_wide_clusters<float, 4>();
+    cudaGetLastError();
+    for (int cs : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(kern::kTailThreads);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern::tail_down<double, 4>, &cfg) == cudaSuccess && n >= 1 &&
+            cudaOccupancyMaxActiveClusters(&n, kern::tail_up<float, 1>, &cfg) == cudaSuccess && n >= 1)
+            return cs;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+float time_cycle(smg_hierarchy* h, bool mixed, cudaEvent_t e0, cudaEvent_t e1) {
+    drop_graphs(h);
+    cudaGraphExec_t g = cycle_graph(h, 1, mixed);
+    ck(cudaGraphLaunch(g, h->cap), "tune launch");
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; rep++) {
+        ck(cudaEventRecord(e0, h->cap), "event");
+        ck(cudaGraphLaunch(g, h->cap), "tune launch");
+        ck(cudaEventRecord(e1, h->cap), "event");
+        ck(cudaEventSynchronize(e1), "event sync");
+        float t = 0.f;
+        ck(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+        best = std::min(best, t);
+    }
+    return best;
+}
+
+// First level handled by the cluster tail, per precision: the fastest cycle
+// over the candidates (levels of at most 300k rows), or a size rule without tuning.
+void choose_tail(smg_hierarchy* h, bool tune) {
+    h->tail64 = h->tail32 = h->H;
+    if (h->tail_cluster == 0 || h->H == 0) return;
+    if (const char* env = std::getenv("SMG_TAIL_LEVEL")) {
+        const int t = std::atoi(env);
+        h->tail64 = h->tail32 = std::max(0, std::min(t, h->H));
+        return;
+    }
+    if (!tune) {
+        for (int l = h->H - 1; l >= 0 && h->L[l].nflat <= 2000000; l--) h->tail64 = l;
+        for (int l = h->H - 1; l >= 1 && h->L[l].nflat <= 6000000; l--) h->tail32 = l;
+        return;
+    }
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0), "event");
+    ck(cudaEventCreate(&e1), "event");
+    const bool trace = std::getenv("SMG_TRACE_TUNE") != nullptr;
+    for (int prec = 0; prec < 2; prec++) {
+        int& t = prec == 0 ? h->tail64 : h->tail32;
+        t = h->H;
+        float best = time_cycle(h, prec == 1, e0, e1);
+        if (trace) std::fprintf(stderr, "[smg tune] %s cycle, no tail: %.1f us\n", prec ? "f32" : "f64", best * 1e3f);
+        int bestT = h->H;
+        for (int cand = h->H - 1; cand >= 0 && h->L[cand].n <= 300000; cand--) {
+            t = cand;
+            const float ms = time_cycle(h, prec == 1, e0, e1);
+            if (trace)
+                std::fprintf(stderr, "[smg tune] %s cycle, tail from level %d: %.1f us\n", prec ? "f32" : "f64", cand,
+                             ms * 1e3f);
+            if (ms < best * 0.97f) {
+                best = ms;
+                bestT = cand;
+            }
+        }
+        t = bestT;
+    }
+    drop_graphs(h);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
 }
 
 // Galerkin chain, level preparation and the coarsest factor, as one graph.
@@ -439,6 +592,8 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
         L.x32 = dalloc<float>(h, L.n * kMaxRhs);
         L.b32 = dalloc<float>(h, L.n * kMaxRhs);
         L.r32 = dalloc<float>(h, L.n * kMaxRhs);
+        for (double* p : {L.x, L.b, L.r}) ck(cudaMemset(p, 0, sizeof(double) * L.n * kMaxRhs), "memset");
+        for (float* p : {L.x32, L.b32, L.r32}) ck(cudaMemset(p, 0, sizeof(float) * L.n * kMaxRhs), "memset");
         if (L.coarsest) {
             L.np = (L.n + kDenseNB - 1) / kDenseNB * kDenseNB;
             L.chol = dalloc<double>(h, L.np * L.np);
@@ -449,13 +604,18 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
             for (auto& e : h->ev_step) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
             ck(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event");
             L.y = dalloc<double>(h, L.n * kMaxRhs);
+            for (double* p : {L.chol, L.linv, L.linvT}) ck(cudaMemset(p, 0, sizeof(double) * L.np * L.np), "memset");
             continue;
         }
         L.slices = upload(h, lp.slices);
         L.sell_col = upload(h, lp.sell_col);
+        L.colour_slice_dev = upload(h, lp.colour_slice);
         L.dinv = dalloc<double>(h, L.n);
         L.vals32 = dalloc<float>(h, L.nflat);
         L.dinv32 = dalloc<float>(h, L.n);
+        ck(cudaMemset(L.dinv, 0, sizeof(double) * L.n), "memset");
+        ck(cudaMemset(L.vals32, 0, sizeof(float) * L.nflat), "memset");
+        ck(cudaMemset(L.dinv32, 0, sizeof(float) * L.n), "memset");
         L.p_idx = upload(h, lp.p_idx);
         L.p_w = upload(h, lp.p_w);
         L.p_w32 = upload(h, to_f32(lp.p_w));
@@ -488,8 +648,18 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
     ck(cudaMemset(h->state, 0, sizeof(SolveState)), "memset");
     h->partials = dalloc<double>(h, (int64_t)kern::kNormBlocks * 2 * kMaxRhs);
     ck(cudaMallocHost((void**)&h->state_host, sizeof(SolveState)), "cudaMallocHost");
+    if (h->H > 0) {
+        std::vector<TailLevel<double>> t64 = tail_table<double>(h);
+        std::vector<TailLevel<float>> t32 = tail_table<float>(h);
+        h->tail_lv64 = dalloc<TailLevel<double>>(h, h->H);
+        h->tail_lv32 = dalloc<TailLevel<float>>(h, h->H);
+        ck(cudaMemcpy(h->tail_lv64, t64.data(), sizeof(TailLevel<double>) * h->H, cudaMemcpyHostToDevice), "upload");
+        ck(cudaMemcpy(h->tail_lv32, t32.data(), sizeof(TailLevel<float>) * h->H, cudaMemcpyHostToDevice), "upload");
+    }
+    h->tail_cluster = detect_tail_cluster();
     ck(cudaDeviceSynchronize(), "upload");
     choose_lanes(h, P, o.autotune != 0);
+    choose_tail(h, o.autotune != 0);
     build_update_graph(h);
     ck(cudaDeviceSynchronize(), "setup");
 }
@@ -797,6 +967,15 @@ int smg_level_config(const smg_hierarchy* h, int level, int32_t out[4]) {
     out[1] = L.R32;
     out[2] = L.ncolours;
     out[3] = L.nslices;
+    return SMG_OK;
+}
+
+int smg_cycle_config(const smg_hierarchy* h, int32_t out[4]) {
+    if (!h || !out) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    out[0] = h->H;
+    out[1] = h->tail64;
+    out[2] = h->tail32;
+    out[3] = h->tail_cluster;
     return SMG_OK;
 }
 

@@ -32,6 +32,7 @@ struct DLevel {
     int ncolours = 0, nslices = 0;
     int R = 1;    // lanes per row of the binary64 kernels
     int R32 = 1;  // lanes per row of the binary32 kernels
+    int32_t* colour_slice_dev = nullptr;
     std::vector<int32_t> colour_slice;  // host copy, ncolours + 1
     SliceMeta* slices = nullptr;
     int32_t* sell_col = nullptr;
@@ -96,6 +97,11 @@ struct smg_hierarchy {
     std::vector<void*> allocs;
     int64_t bytes = 0;
     int device = 0;
+    // cluster tail: levels [tail, H) of a cycle run in one thread-block cluster
+    void* tail_lv64 = nullptr;  // TailLevel<double>[H]
+    void* tail_lv32 = nullptr;  // TailLevel<float>[H]
+    int tail64 = 0, tail32 = 0;  // first tail level per precision (H = no tail)
+    int tail_cluster = 0;        // CTAs per tail cluster (0 = clusters unavailable)
 };
 
 namespace smg {
@@ -107,6 +113,28 @@ void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s);
 // dependents (they wait for the preceding kernel before reading `in`).
 void record_coarsest_solve(smg_hierarchy* h, int K, const void* in, bool in32, void* out, bool out32,
                            cudaStream_t s);
+// Cluster launch (grid = one cluster of `cluster` CTAs) with programmatic stream
+// serialization; the kernel must call griddepcontrol.wait before dependent reads.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_cluster_pdl(void (*kernel)(Params...), int cluster, dim3 block, cudaStream_t s,
+                                      Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Launch with programmatic stream serialization: under stream capture the edge to
 // the previous kernel becomes a programmatic dependency, so this kernel may start
 // before its predecessor finishes and must call griddepcontrol.wait before

@@ -23,6 +23,14 @@ __device__ __forceinline__ T ldg(const T* p) {
     return __ldg(p);
 }
 
+// Loads of data that other CTAs of the same launch write (cluster tail kernels):
+// served by L2, the coherence point, never by the non-coherent read-only path.
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+    if (COHERENT) return __ldcg(p);
+    return __ldg(p);
+}
+
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch.  Kernels of a cycle are launched so that the
 // next kernel may start while the previous one drains: everything a kernel
@@ -64,7 +72,9 @@ struct RowSlice {
             }
         }
     }
-    // x may be written by this launch at other rows only, or read-only
+    // COHERENT = false: x is read-only in this launch except at rows this warp
+    // owns; true: other CTAs of this launch write x between cluster barriers
+    template <bool COHERENT = false>
     __device__ __forceinline__ void dot(const SliceMeta& m, const int32_t* __restrict__ col,
                                         const T* __restrict__ sval, const T* x, T (&acc)[K]) const {
         T xv[PRE][K];
@@ -72,7 +82,7 @@ struct RowSlice {
         for (int u = 0; u < PRE; u++)
             if (sub + R * u < W)
 #pragma unroll
-                for (int q = 0; q < K; q++) xv[u][q] = ldg(x + (int64_t)c[u] * K + q);
+                for (int q = 0; q < K; q++) xv[u][q] = ldx<COHERENT>(x + (int64_t)c[u] * K + q);
 #pragma unroll
         for (int q = 0; q < K; q++) acc[q] = T(0);
 #pragma unroll
@@ -84,7 +94,7 @@ struct RowSlice {
             const int cc = ldg(col + m.off + k * 32 + r);
             const T vv = ldg(sval + m.off + k * 32 + r);
 #pragma unroll
-            for (int q = 0; q < K; q++) acc[q] -= vv * ldg(x + (int64_t)cc * K + q);
+            for (int q = 0; q < K; q++) acc[q] -= vv * ldx<COHERENT>(x + (int64_t)cc * K + q);
         }
 #pragma unroll
         for (int o = 16; o >= RL; o >>= 1)

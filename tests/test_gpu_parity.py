@@ -192,3 +192,28 @@ def test_error_statuses(ico):
     _, info = h.solve(b, check=False)
     assert info["return"] == 5 and info["cycles"] == 2
     h.close()
+
+
+@pytest.mark.parametrize("tail", ["0", "1", "99"])
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_cluster_tail_and_launch_paths_match_oracle(tail, nrhs, monkeypatch):
+    """Level 0 onwards inside the cluster tail ("0"), levels >= 1 ("1"), and no
+    tail ("99" clamps to H): every cycle iterate must match the oracle."""
+    monkeypatch.setenv("SMG_TAIL_LEVEL", tail)
+    V, F = synth.torus(64, 32, seed=3)
+    c = Case(V, F, 1e-3, min_coarse=100)
+    H, t64, t32, ctas = c.h.cycle_config()
+    assert t64 == min(int(tail), H) or ctas == 0
+    b = synth.uniform_rhs(c.n, nrhs=nrhs, seed=12)
+    x_or = np.zeros_like(b)
+    x_gpu = to_dev(x_or.copy())
+    bd = to_dev(b)
+    for k in range(4):
+        x_or = oracle.vcycle(c.levels, 0, np.ascontiguousarray(x_or), b, oracle.Options())
+        c.h.vcycle(bd, x_gpu)
+        assert rel(x_gpu.cpu().numpy(), x_or) <= CYCLE_TOL, k
+    c.h.set_options(rtol=1e-10, precision=smg.MIXED)
+    x, info = c.h.solve(bd)
+    assert info["return"] == 0
+    assert oracle.rel_residual(c.A, x.cpu().numpy(), b) <= 1e-10
+    c.h.close()
