@@ -256,6 +256,32 @@ int  smg_level_config(const smg_hierarchy *h, int level, int32_t out[4]);
  * cluster (0 when the device offers no cluster launch). */
 int  smg_cycle_config(const smg_hierarchy *h, int32_t out[4]);
 
+/*
+ * Residual norms of a system the caller holds, with no allocation at all.
+ * (The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory when they need it -- code running during CUDA graph
+ * capture, where cudaMalloc is not allowed; real-time loops that must not wait
+ * on an allocator; hosts that own every device allocation of a plug-in.)
+ *   rowptr_dev  n + 1 row offsets (int64), col_dev / vals_dev the CSR entries
+ *               (any order inside a row), all on the device
+ *   x_dev, b_dev  n x nrhs row-major, nrhs in 1..4
+ *   out_dev     2 nrhs doubles: out[q] = ||b_q - A x_q||_2^2, out[nrhs + q] =
+ *               ||b_q||_2^2, written in stream order on `stream`
+ * Nothing is allocated: the partial sums of the reduction live in a fixed
+ * device array inside the library (608 x 8 doubles, 38 KB), resident on every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks that array up (cudaGetSymbolAddress); make that first call
+ * before capturing a stream.  Every call on a device shares the array, so
+ * calls whose work may overlap on the GPU (different streams without
+ * ordering) race and must be serialised by the caller.  The reduction order is
+ * fixed: repeated calls on the same data return identical bits.
+ * Returns SMG_ERR_INVALID_ARG for nrhs outside 1..4, n < 1 or a null pointer,
+ * SMG_ERR_CUDA if the launch fails.
+ */
+int  smg_residual_norms_noalloc(int64_t n, const int64_t *rowptr_dev, const int32_t *col_dev,
+                                const double *vals_dev, const double *x_dev, const double *b_dev,
+                                int nrhs, double *out_dev, smg_stream stream);
+
 /* Device bytes held by the hierarchy. */
 int64_t smg_device_bytes(const smg_hierarchy *h);
 

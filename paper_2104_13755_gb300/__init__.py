@@ -88,6 +88,7 @@ def _load():
         "smg_level_config": (I32, [P, I32, P]),
         "smg_cycle_config": (I32, [P, P]),
         "smg_device_bytes": (I64, [P]),
+        "smg_residual_norms_noalloc": (I32, [I64, P, P, P, P, P, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
