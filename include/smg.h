@@ -282,6 +282,29 @@ int  smg_residual_norms_noalloc(int64_t n, const int64_t *rowptr_dev, const int3
                                 const double *vals_dev, const double *x_dev, const double *b_dev,
                                 int nrhs, double *out_dev, smg_stream stream);
 
+/* =====================================================================
+ * Batches: many meshes (each with its own hierarchy) updated and solved by
+ * one graph launch each, a branch per mesh, so the small coarse-level kernels
+ * of different meshes overlap on the GPU.
+ * ===================================================================== */
+typedef struct smg_batch smg_batch;
+
+/* Reference `count` hierarchies of the current device (they must outlive the
+ * batch; options of a hierarchy are read when the batch first uses it). */
+int  smg_batch_create(smg_hierarchy *const *hierarchies, int count, smg_batch **out);
+void smg_batch_destroy(smg_batch *batch);
+/* Offsets of mesh i in the concatenated vectors: unknowns [u[i], u[i+1]),
+ * vertices [v[i], v[i+1]) (host arrays of count + 1). */
+int  smg_batch_offsets(const smg_batch *batch, int64_t *unknown_offsets, int64_t *vertex_offsets);
+/* smg_update_positions for every mesh: V_dev holds the meshes' positions
+ * concatenated (vertex offsets x 3), one t for all. */
+int  smg_batch_update_positions(smg_batch *batch, const double *V_dev, double t, smg_stream stream);
+/* Solve every mesh: b_dev, x_dev concatenated (unknown offsets x nrhs,
+ * row-major per mesh); infos (count entries) may be NULL.  Synchronises
+ * `stream`; returns the first failing status over the meshes or SMG_OK. */
+int  smg_batch_solve(smg_batch *batch, const double *b_dev, double *x_dev, int nrhs, smg_info *infos,
+                     smg_stream stream);
+
 /* Device bytes held by the hierarchy. */
 int64_t smg_device_bytes(const smg_hierarchy *h);
 

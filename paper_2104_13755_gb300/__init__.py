@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Plan", "Hierarchy", "SmgError", "Options", "Info", "FP64", "MIXED", "lib", "library_path"]
+__all__ = ["Plan", "Hierarchy", "Batch", "SmgError", "Options", "Info", "FP64", "MIXED", "lib", "library_path"]
 
 FP64, MIXED = 0, 1
 
@@ -89,6 +89,11 @@ def _load():
         "smg_cycle_config": (I32, [P, P]),
         "smg_device_bytes": (I64, [P]),
         "smg_residual_norms_noalloc": (I32, [I64, P, P, P, P, P, I32, P, P]),
+        "smg_batch_create": (I32, [P, I32, P]),
+        "smg_batch_destroy": (None, [P]),
+        "smg_batch_offsets": (I32, [P, P, P]),
+        "smg_batch_update_positions": (I32, [P, P, D, P]),
+        "smg_batch_solve": (I32, [P, P, P, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -360,3 +365,47 @@ class Hierarchy:
     @property
     def device_bytes(self):
         return lib.smg_device_bytes(self._h)
+
+
+class Batch:
+    """Several hierarchies (same device) updated and solved by one graph launch
+    each, one graph branch per mesh (smg_batch_*).  Vectors are the meshes'
+    unknown vectors concatenated; positions the meshes' vertices concatenated."""
+
+    def __init__(self, hierarchies):
+        self.hs = list(hierarchies)
+        arr = (ctypes.c_void_p * len(self.hs))(*[h._h.value for h in self.hs])
+        self._h = ctypes.c_void_p()
+        _check(lib.smg_batch_create(arr, len(self.hs), ctypes.byref(self._h)), "smg_batch_create")
+        u = (ctypes.c_int64 * (len(self.hs) + 1))()
+        v = (ctypes.c_int64 * (len(self.hs) + 1))()
+        _check(lib.smg_batch_offsets(self._h, u, v), "smg_batch_offsets")
+        self.unknown_offsets = list(u)
+        self.vertex_offsets = list(v)
+
+    def close(self):
+        if self._h:
+            lib.smg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update_positions(self, V, t, stream=None):
+        _check(lib.smg_batch_update_positions(self._h, _dev_ptr(V), float(t), _stream_ptr(stream)),
+               "smg_batch_update_positions")
+
+    def solve(self, b, x=None, stream=None, check=True):
+        """Solve every mesh; returns (x, list of info dicts)."""
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        infos = (Info * len(self.hs))()
+        st = lib.smg_batch_solve(self._h, _dev_ptr(b), _dev_ptr(x), nrhs, infos, _stream_ptr(stream))
+        if check and st != 0:
+            _check(st, "smg_batch_solve")
+        return x, [i.as_dict() for i in infos]

@@ -1,6 +1,7 @@
 // Device hierarchy: upload, update (assembly + Galerkin + coarsest factor),
 // graph-captured V-cycles and the device half of the C ABI.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -227,15 +228,18 @@ void rec_final(smg_hierarchy* h, cudaGraphConditionalHandle hnd, bool init, bool
        "norm final");
 }
 
+// Append to graph g an independent branch solving one system: optional
+// prologue, ||b|| and the first stopping test, a WHILE node running one cycle
+// + residual norm + stopping test per iteration, optional epilogue after the
+// loop.  Captured on `s`; the branch has no dependency on other nodes of g.
 template <int K>
-cudaGraphExec_t build_solve_graph(smg_hierarchy* h, bool mixed) {
-    cudaStream_t s = h->cap;
-    cudaGraph_t g = nullptr;
-    ck(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+void add_solve_branch(smg_hierarchy* h, cudaGraph_t g, cudaStream_t s, bool mixed,
+                      const std::function<void(cudaStream_t)>& prologue,
+                      const std::function<void(cudaStream_t)>& epilogue) {
     cudaGraphConditionalHandle hnd;
     ck(cudaGraphConditionalHandleCreate(&hnd, g, 0, 0), "cudaGraphConditionalHandleCreate");
-    // before the loop: ||b||, the initial residual and the first stopping test
     ck(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), "capture init");
+    if (prologue) prologue(s);
     rec_resnorm<K>(h, true, mixed, s);
     rec_final<K>(h, hnd, true, true, s);
     cudaStreamCaptureStatus cst;
@@ -244,8 +248,8 @@ cudaGraphExec_t build_solve_graph(smg_hierarchy* h, bool mixed) {
     ck(cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps), "capture info");
     std::vector<cudaGraphNode_t> frontier(deps, deps + ndeps);
     ck(cudaGetLastError(), "init launches");
-    ck(cudaStreamEndCapture(s, &g), "end capture init");
-    // WHILE node: one cycle, the residual norm and the stopping test per iteration
+    cudaGraph_t gg = g;
+    ck(cudaStreamEndCapture(s, &gg), "end capture init");
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = hnd;
@@ -261,6 +265,20 @@ cudaGraphExec_t build_solve_graph(smg_hierarchy* h, bool mixed) {
     rec_final<K>(h, hnd, false, true, s);
     ck(cudaGetLastError(), "body launches");
     ck(cudaStreamEndCapture(s, &body), "end capture body");
+    if (epilogue) {
+        ck(cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal), "capture epilogue");
+        epilogue(s);
+        ck(cudaGetLastError(), "epilogue launches");
+        gg = g;
+        ck(cudaStreamEndCapture(s, &gg), "end capture epilogue");
+    }
+}
+
+template <int K>
+cudaGraphExec_t build_solve_graph(smg_hierarchy* h, bool mixed) {
+    cudaGraph_t g = nullptr;
+    ck(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    add_solve_branch<K>(h, g, h->cap, mixed, nullptr, nullptr);
     cudaGraphExec_t exec = nullptr;
     ck(cudaGraphInstantiate(&exec, g, 0), "instantiate solve graph");
     cudaGraphDestroy(g);
@@ -520,11 +538,8 @@ void choose_tail(smg_hierarchy* h, bool tune) {
     cudaEventDestroy(e1);
 }
 
-// Galerkin chain, level preparation and the coarsest factor, as one graph.
-void build_update_graph(smg_hierarchy* h) {
-    cudaStream_t s = h->cap;
-    cudaGraph_t g = nullptr;
-    ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture update");
+// Galerkin chain, level preparation and the coarsest factor.
+void rec_update(smg_hierarchy* h, cudaStream_t s) {
     ck(cudaMemsetAsync(&h->state->chol_bad, 0, sizeof(int32_t), s), "memset");
     for (int l = 0; l < h->H; l++) {
         DLevel& L = h->L[l];
@@ -537,6 +552,27 @@ void build_update_graph(smg_hierarchy* h) {
                                                                       L.dinv32);
     }
     record_coarsest_factor(h, s);
+}
+
+// Level-0 assembly A = M + t L from positions V (t from device memory).
+void rec_assembly(smg_hierarchy* h, const double* V, const double* t_dev, cudaStream_t s) {
+    DLevel& L0 = h->L[0];
+    const int64_t dense_n = L0.coarsest ? L0.n : 0;
+    kern::face_geom<<<blocks_for(h->nf), kern::kThreads, 0, s>>>(h->nf, h->F, V, h->facegeom);
+    kern::asm_diag<<<blocks_for(L0.n), kern::kThreads, 0, s>>>(L0.n, L0.coarsest ? L0.n + 1 : 1, h->inc_ptr,
+                                                               h->inc_code, h->facegeom, h->Lflat0, h->Mdiag);
+    const int64_t first = L0.coarsest ? 0 : L0.sbase;
+    kern::asm_off<<<blocks_for(L0.nflat - first), kern::kThreads, 0, s>>>(L0.nflat, first, dense_n, h->opp0, h->opp1,
+                                                                          h->facegeom, h->Lflat0);
+    kern::combine_devt<<<blocks_for(L0.nflat), kern::kThreads, 0, s>>>(L0.nflat, L0.n, dense_n, t_dev, h->Lflat0,
+                                                                       h->Mdiag, L0.vals);
+}
+
+void build_update_graph(smg_hierarchy* h) {
+    cudaStream_t s = h->cap;
+    cudaGraph_t g = nullptr;
+    ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture update");
+    rec_update(h, s);
     ck(cudaGetLastError(), "update launches");
     ck(cudaStreamEndCapture(s, &g), "end capture update");
     ck(cudaGraphInstantiate(&h->update_exec, g, 0), "instantiate update graph");
@@ -662,6 +698,68 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
     choose_tail(h, o.autotune != 0);
     build_update_graph(h);
     ck(cudaDeviceSynchronize(), "setup");
+}
+
+template <class T>
+T* balloc(smg_batch* b, int64_t count) {
+    if (count <= 0) count = 1;
+    void* p = nullptr;
+    ck(cudaMalloc(&p, sizeof(T) * (size_t)count), "cudaMalloc");
+    b->allocs.push_back(p);
+    return (T*)p;
+}
+
+void build_batch_update(smg_batch* B) {
+    cudaGraph_t g = nullptr;
+    ck(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    for (size_t i = 0; i < B->hs.size(); i++) {
+        smg_hierarchy* h = B->hs[i];
+        ck(cudaStreamBeginCaptureToGraph(B->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+           "capture batch update");
+        rec_assembly(h, B->stage_V + 3 * B->voff[i], B->t_dev, B->cap);
+        rec_update(h, B->cap);
+        ck(cudaGetLastError(), "batch update launches");
+        cudaGraph_t gg = g;
+        ck(cudaStreamEndCapture(B->cap, &gg), "end capture batch update");
+    }
+    ck(cudaGraphInstantiate(&B->update_exec, g, 0), "instantiate batch update");
+    cudaGraphDestroy(g);
+}
+
+template <int K>
+cudaGraphExec_t build_batch_solve(smg_batch* B, bool mixed) {
+    cudaGraph_t g = nullptr;
+    ck(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    for (size_t i = 0; i < B->hs.size(); i++) {
+        smg_hierarchy* h = B->hs[i];
+        DLevel& L0 = h->L[0];
+        const int64_t m = L0.n * K;
+        const double* bsrc = B->stage_b + B->uoff[i] * K;
+        double* xsrc = B->stage_x + B->uoff[i] * K;
+        smg::SolveState* dst = B->states + i;
+        auto pro = [&](cudaStream_t s) {
+            kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, K, h->perm0, bsrc, L0.b);
+            kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, K, h->perm0, xsrc, L0.x);
+        };
+        auto epi = [&](cudaStream_t s) {
+            kern::scatter_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, K, h->perm0, L0.x, xsrc);
+            ck(cudaMemcpyAsync(dst, h->state, sizeof(smg::SolveState), cudaMemcpyDeviceToHost, s), "state copy");
+        };
+        add_solve_branch<K>(h, g, B->cap, mixed, pro, epi);
+    }
+    cudaGraphExec_t exec = nullptr;
+    ck(cudaGraphInstantiate(&exec, g, 0), "instantiate batch solve");
+    cudaGraphDestroy(g);
+    return exec;
+}
+
+void free_batch(smg_batch* B) {
+    if (B->update_exec) cudaGraphExecDestroy(B->update_exec);
+    for (auto& kv : B->solve_exec) cudaGraphExecDestroy(kv.second);
+    for (void* p : B->allocs) cudaFree(p);
+    if (B->t_host) cudaFreeHost(B->t_host);
+    if (B->states) cudaFreeHost(B->states);
+    if (B->cap) cudaStreamDestroy(B->cap);
 }
 
 int fail(const std::string& msg, int code) {
@@ -977,6 +1075,122 @@ int smg_cycle_config(const smg_hierarchy* h, int32_t out[4]) {
     out[2] = h->tail32;
     out[3] = h->tail_cluster;
     return SMG_OK;
+}
+
+int smg_batch_create(smg_hierarchy* const* hs, int count, smg_batch** out) {
+    if (!hs || count < 1 || !out) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail("no current device", SMG_ERR_CUDA);
+    for (int i = 0; i < count; i++)
+        if (!hs[i] || hs[i]->device != dev) return fail("null hierarchy or one of another device", SMG_ERR_INVALID_ARG);
+    smg_batch* B = new (std::nothrow) smg_batch();
+    if (!B) return SMG_ERR_NO_MEMORY;
+    try {
+        B->device = dev;
+        B->hs.assign(hs, hs + count);
+        B->uoff.assign(count + 1, 0);
+        B->voff.assign(count + 1, 0);
+        for (int i = 0; i < count; i++) {
+            B->uoff[i + 1] = B->uoff[i] + hs[i]->nu;
+            B->voff[i + 1] = B->voff[i] + hs[i]->nv;
+        }
+        ck(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+        B->stage_b = balloc<double>(B, B->uoff[count] * kMaxRhs);
+        B->stage_x = balloc<double>(B, B->uoff[count] * kMaxRhs);
+        B->stage_V = balloc<double>(B, B->voff[count] * 3);
+        B->t_dev = balloc<double>(B, 1);
+        ck(cudaMallocHost((void**)&B->t_host, sizeof(double)), "cudaMallocHost");
+        ck(cudaMallocHost((void**)&B->states, sizeof(SolveState) * count), "cudaMallocHost");
+        build_batch_update(B);
+    } catch (const CudaFail& e) {
+        free_batch(B);
+        delete B;
+        cudaGetLastError();
+        return fail(e.what(), SMG_ERR_CUDA);
+    } catch (const std::bad_alloc&) {
+        free_batch(B);
+        delete B;
+        return fail("host allocation failed", SMG_ERR_NO_MEMORY);
+    }
+    *out = B;
+    return SMG_OK;
+}
+
+void smg_batch_destroy(smg_batch* B) {
+    if (!B) return;
+    cudaStreamSynchronize(B->cap);
+    free_batch(B);
+    delete B;
+}
+
+int smg_batch_offsets(const smg_batch* B, int64_t* u, int64_t* v) {
+    if (!B) return fail("null batch", SMG_ERR_INVALID_ARG);
+    for (size_t i = 0; i < B->uoff.size(); i++) {
+        if (u) u[i] = B->uoff[i];
+        if (v) v[i] = B->voff[i];
+    }
+    return SMG_OK;
+}
+
+int smg_batch_update_positions(smg_batch* B, const double* V, double t, smg_stream stream) {
+    if (!B || !V) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (!std::isfinite(t)) return fail("t must be finite", SMG_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    ck(cudaMemcpyAsync(B->stage_V, V, sizeof(double) * 3 * B->voff.back(), cudaMemcpyDeviceToDevice, s), "copy V");
+    ck(cudaStreamSynchronize(s), "sync");  // t_host is reused by the next call
+    *B->t_host = t;
+    ck(cudaMemcpyAsync(B->t_dev, B->t_host, sizeof(double), cudaMemcpyHostToDevice, s), "copy t");
+    ck(cudaGraphLaunch(B->update_exec, s), "batch update");
+    for (smg_hierarchy* h : B->hs) h->have_positions = h->have_matrix = true;
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_batch_solve(smg_batch* B, const double* b, double* x, int nrhs, smg_info* infos, smg_stream stream) {
+    if (!B || !b || !x) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (nrhs < 1 || nrhs > kMaxRhs) return fail("nrhs must be 1..4", SMG_ERR_INVALID_ARG);
+    for (smg_hierarchy* h : B->hs)
+        if (!h->have_matrix) return fail("batch solve before any update", SMG_ERR_STATE);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    const bool mixed = B->hs[0]->opts.precision == SMG_MIXED;
+    const int key = (mixed ? 16 : 0) + nrhs;
+    auto it = B->solve_exec.find(key);
+    cudaGraphExec_t e;
+    if (it != B->solve_exec.end()) e = it->second;
+    else {
+        switch (nrhs) {
+            case 1: e = build_batch_solve<1>(B, mixed); break;
+            case 2: e = build_batch_solve<2>(B, mixed); break;
+            case 3: e = build_batch_solve<3>(B, mixed); break;
+            default: e = build_batch_solve<4>(B, mixed); break;
+        }
+        B->solve_exec[key] = e;
+    }
+    const size_t bytes = sizeof(double) * (size_t)(B->uoff.back() * nrhs);
+    ck(cudaMemcpyAsync(B->stage_b, b, bytes, cudaMemcpyDeviceToDevice, s), "copy b");
+    ck(cudaMemcpyAsync(B->stage_x, x, bytes, cudaMemcpyDeviceToDevice, s), "copy x");
+    ck(cudaGraphLaunch(e, s), "batch solve");
+    ck(cudaMemcpyAsync(x, B->stage_x, bytes, cudaMemcpyDeviceToDevice, s), "copy x back");
+    ck(cudaStreamSynchronize(s), "sync");
+    int worst = SMG_OK;
+    for (size_t i = 0; i < B->hs.size(); i++) {
+        const SolveState& ss = B->states[i];
+        if (infos) {
+            infos[i].cycles = ss.cycles;
+            infos[i].status = ss.status;
+            infos[i].rel_residual0 = ss.rel0;
+            infos[i].rel_residual = ss.rel;
+            infos[i].rho = (ss.cycles > 0 && ss.rel0 > 0) ? std::pow(ss.rel / ss.rel0, 1.0 / ss.cycles) : 0.0;
+        }
+        int st = ss.chol_bad ? SMG_ERR_NOT_SPD : (ss.status < 0 ? SMG_OK : ss.status);
+        if (worst == SMG_OK && st != SMG_OK) worst = st;
+    }
+    if (worst != SMG_OK) return fail("a mesh of the batch did not converge or was not SPD", worst);
+    return SMG_OK;
+    SMG_GUARD_END
 }
 
 int64_t smg_device_bytes(const smg_hierarchy* h) { return h ? h->bytes : 0; }

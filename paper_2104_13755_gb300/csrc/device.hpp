@@ -104,6 +104,23 @@ struct smg_hierarchy {
     int tail_cluster = 0;        // CTAs per tail cluster (0 = clusters unavailable)
 };
 
+// Several hierarchies solved by one graph launch (a branch per mesh).
+struct smg_batch {
+    std::vector<smg_hierarchy*> hs;        // referenced, owned by the caller
+    std::vector<int64_t> uoff, voff;       // unknown / vertex offsets of the concatenated vectors
+    double* stage_b = nullptr;             // concatenated user-order right-hand sides (x kMaxRhs)
+    double* stage_x = nullptr;             // concatenated user-order iterates (x kMaxRhs)
+    double* stage_V = nullptr;             // concatenated positions
+    double* t_dev = nullptr;
+    double* t_host = nullptr;              // pinned
+    smg::SolveState* states = nullptr;     // pinned, one per mesh
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t update_exec = nullptr;
+    std::map<int, cudaGraphExec_t> solve_exec;
+    std::vector<void*> allocs;
+    int device = 0;
+};
+
 namespace smg {
 // dense.cu: record the coarsest factorisation (Cholesky, then the inverse factor
 // and its transpose) on `s`; launches only, capturable.

@@ -480,6 +480,21 @@ __global__ void combine(int64_t nflat, int64_t n, int64_t dense_n, double t, con
     vals[e] = v;
 }
 
+// The same with t read from device memory (graph-captured batch updates).
+__global__ void combine_devt(int64_t nflat, int64_t n, int64_t dense_n, const double* __restrict__ t,
+                             const double* __restrict__ Lflat, const double* __restrict__ M,
+                             double* __restrict__ vals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nflat) return;
+    double v = t[0] * Lflat[e];
+    if (dense_n > 0) {
+        if (e / dense_n == e % dense_n) v += M[e / dense_n];
+    } else if (e < n) {
+        v += M[e];
+    }
+    vals[e] = v;
+}
+
 // User-supplied level-0 values (natural CSR) scattered to the flat layout.
 __global__ void scatter_user(int64_t nflat, const int64_t* __restrict__ map, const double* __restrict__ user,
                              double* __restrict__ vals) {

@@ -217,3 +217,42 @@ def test_cluster_tail_and_launch_paths_match_oracle(tail, nrhs, monkeypatch):
     assert info["return"] == 0
     assert oracle.rel_residual(c.A, x.cpu().numpy(), b) <= 1e-10
     c.h.close()
+
+
+def test_batch_matches_individual_solves_and_oracle():
+    """a11: uneven meshes (spheres, tori, a Dirichlet disk) with 3 right-hand
+    sides each, updated and solved by one graph launch; every mesh must equal
+    its own stand-alone solve and the oracle."""
+    meshes = [synth.perturbed_icosphere(3, seed=1), synth.torus(48, 20, seed=2),
+              synth.perturbed_geodesic_sphere(14, seed=3), synth.torus(90, 30, seed=4)]
+    Vd, Fd, bnd = synth.disk(40, seed=5)
+    cases = []
+    for V, F in meshes:
+        cases.append(Case(V, F, 1e-2, max_coarse=300))
+    cases.append(Case(Vd, Fd, 1e-2, mask=bnd, max_coarse=300))
+    batch = smg.Batch([c.h for c in cases])
+    Vcat = torch.from_numpy(np.concatenate([c.V for c in cases])).cuda()
+    batch.update_positions(Vcat, 1e-2)
+    bs = [synth.uniform_rhs(c.n, nrhs=3, seed=20 + i) for i, c in enumerate(cases)]
+    for prec in (smg.FP64, smg.MIXED):
+        for c in cases:
+            c.h.set_options(rtol=1e-10, precision=prec)
+        batch.close()
+        batch = smg.Batch([c.h for c in cases])
+        batch.update_positions(Vcat, 1e-2)
+        x, infos = batch.solve(to_dev(np.concatenate(bs)))
+        xs = x.cpu().numpy()
+        u = batch.unknown_offsets
+        for i, c in enumerate(cases):
+            xi = xs[u[i]:u[i + 1]]
+            single, info = c.h.solve(to_dev(bs[i]))
+            assert infos[i]["cycles"] == info["cycles"]
+            assert np.array_equal(xi, single.cpu().numpy())      # same kernels, same bits
+            assert oracle.rel_residual(c.A, xi, bs[i]) <= 1e-10
+            if prec == smg.FP64:
+                ref = oracle.solve(c.levels, bs[i], opt=oracle.Options(rtol=1e-10))
+                assert infos[i]["cycles"] == ref.cycles
+                assert rel(xi, ref.x) <= CYCLE_TOL
+    for c in cases:
+        c.h.set_options(rtol=1e-10, precision=smg.FP64)
+    batch.close()
