@@ -219,6 +219,26 @@ int  smg_vcycle(smg_hierarchy *h, const double *b_dev, double *x_dev, int nrhs, 
 int  smg_mass(smg_hierarchy *h, double *m_dev, smg_stream stream);
 int  smg_apply_mass(smg_hierarchy *h, const double *x_dev, double *y_dev, int nrhs, smg_stream stream);
 
+/*
+ * Derivatives for the differentiable solve x = A(V, t)^{-1} b (the adjoint
+ * form): with lambda = A^{-1} g for an upstream gradient g (a second
+ * smg_solve, A being symmetric), dl/db = lambda, and
+ *   smg_operator_grad: gradV_dev (all n vertices x 3) = -d/dV sum_q lambda_q^T A(V,t) x_q
+ *                      and dt_dev[0] = -sum_q lambda_q^T L x_q (dt_dev may be NULL);
+ *                      lambda_dev, x_dev: unknowns x nrhs; V_dev: the positions of A.
+ *   smg_lumped_mass:   m_dev (unknowns) = lumped mass of positions V_dev.
+ *   smg_mass_grad:     gradV_dev = d/dV (w^T m(V)) for w_dev over the unknowns.
+ * Known (Dirichlet) vertices count as zero in lambda, x and w.  Per-face
+ * analytic derivatives of the areas and cotangents, gathered per vertex in a
+ * fixed order (reproducible).  The first derivative call allocates 80 bytes
+ * per face of scratch.  Asynchronous on `stream`.
+ */
+int  smg_operator_grad(smg_hierarchy *h, const double *V_dev, double t, const double *lambda_dev,
+                       const double *x_dev, int nrhs, double *gradV_dev, double *dt_dev, smg_stream stream);
+int  smg_lumped_mass(smg_hierarchy *h, const double *V_dev, double *m_dev, smg_stream stream);
+int  smg_mass_grad(smg_hierarchy *h, const double *V_dev, const double *w_dev, double *gradV_dev,
+                   smg_stream stream);
+
 /* Copy the values of A_l to the host, aligned with smg_plan_pattern(level)
  * (natural numbering); synchronises `stream`. */
 int  smg_level_matrix(smg_hierarchy *h, int level, double *vals_host, smg_stream stream);

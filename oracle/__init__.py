@@ -393,3 +393,135 @@ def convergence_factor(history):
     if k <= 0 or history[0] == 0:
         return 0.0
     return float((history[-1] / history[0]) ** (1.0 / k))
+
+
+# ---------------------------------------------------------------------------
+# Derivatives for the differentiable solve (form 3; the paper has no adjoint)
+# ---------------------------------------------------------------------------
+# x = A(V, t)^{-1} b.  For a loss l(x): lambda = A^{-1} dl/dx (A symmetric), and
+#   dl/db = lambda,  dl/dt = -lambda^T L x,  dl/dV = -d/dV [lambda^T A(V) x].
+# The position derivatives here are per-face complex-step derivatives
+# (Squire and Trapp 1998: f'(a) = Im f(a + i h) / h, exact to rounding for
+# real-analytic f), so they share no formula with any closed-form derivative
+# of cot or area.  The per-face terms sum over faces because
+#   lambda^T M x = sum_f area_f / 3 * sum_{c in f} lambda_c x_c
+#   lambda^T L x = sum_f sum_k cot_k / 2 * (lambda_i - lambda_j)(x_i - x_j)
+# with edge (i, j) opposite corner k.
+_CS_STEP = 1e-30
+
+
+def _face_energy(P, lv, xv, w, t):
+    """Per-face energy from corner positions P (nf, 3, 3), complex allowed.
+    Operator form (w is None): area/3 sum_c lv_c.xv_c + t sum_k cot_k/2 (dlv).(dxv);
+    mass form: area/3 sum_c w_c.  No abs() anywhere, so complex steps propagate."""
+    def cross(a, b):
+        return np.stack([a[:, 1] * b[:, 2] - a[:, 2] * b[:, 1],
+                         a[:, 2] * b[:, 0] - a[:, 0] * b[:, 2],
+                         a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0]], axis=1)
+
+    def norm(a):
+        return np.sqrt(np.sum(a * a, axis=1))
+
+    area = 0.5 * norm(cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]))
+    if w is not None:
+        return area / 3.0 * w.sum(axis=1)
+    e = area / 3.0 * np.einsum("fcq,fcq->f", lv, xv)
+    for k in range(3):
+        i, j = (k + 1) % 3, (k + 2) % 3
+        u = P[:, i] - P[:, k]
+        v = P[:, j] - P[:, k]
+        cot = np.sum(u * v, axis=1) / norm(cross(u, v))
+        e = e + t * 0.5 * cot * np.einsum("fq,fq->f", lv[:, i] - lv[:, j], xv[:, i] - xv[:, j])
+    return e
+
+
+def _faces_complex_step(V, F, lv, xv, w, t):
+    """d(face energy)/d(corner coordinate) for every face, gathered per vertex."""
+    V = np.asarray(V, dtype=np.float64)
+    F = np.asarray(F, dtype=np.int64)
+    P = V[F]
+    G = np.zeros_like(V)
+    for c in range(3):
+        for d in range(3):
+            Pc = P.astype(np.complex128)
+            Pc[:, c, d] += 1j * _CS_STEP
+            g = _face_energy(Pc, lv, xv, w, t).imag / _CS_STEP
+            np.add.at(G[:, d], F[:, c], g)
+    return G
+
+
+def _per_vertex(a, n, unknowns):
+    """Values on the unknowns (n_u x K) -> per-vertex (n x K), zero on known vertices."""
+    a = np.asarray(a, dtype=np.float64)
+    a = a.reshape(a.shape[0], -1)
+    out = np.zeros((n, a.shape[1]))
+    out[unknowns] = a
+    return out
+
+
+def operator_grad(V, F, t, lam, x, unknowns=None):
+    """(d/dV [lambda^T A(V, t) x] as n x 3, lambda^T L x) with lambda, x given on
+    the unknowns (all vertices when `unknowns` is None); known vertices carry 0."""
+    n = np.asarray(V).shape[0]
+    u = np.arange(n) if unknowns is None else np.asarray(unknowns)
+    lv = _per_vertex(lam, n, u)
+    xv = _per_vertex(x, n, u)
+    F64 = np.asarray(F, dtype=np.int64)
+    G = _faces_complex_step(V, F64, lv[F64], xv[F64], None, t)
+    L = cotan_laplacian(V, F)
+    dt = float(np.sum(lv * (L @ xv)))
+    return G, dt
+
+
+def mass_grad(V, F, w, unknowns=None):
+    """d/dV [w^T m(V)] (n x 3) with m the lumped mass of the unknowns."""
+    n = np.asarray(V).shape[0]
+    u = np.arange(n) if unknowns is None else np.asarray(unknowns)
+    wv = _per_vertex(w, n, u)[:, 0]
+    F64 = np.asarray(F, dtype=np.int64)
+    return _faces_complex_step(V, F64, None, None, wv[F64], 0.0)
+
+
+@dataclass
+class HeatLossResult:
+    loss: float
+    x: np.ndarray
+    lam: np.ndarray
+    dV: np.ndarray       # n x 3
+    dt: float
+    db: np.ndarray       # on the unknowns
+
+
+def heat_loss_grad(V, F, t, known, s):
+    """l = x^T M x with A x = b, b = M e_s (unit impulse at unknown s), all on the
+    Dirichlet-reduced unknowns (zero values on the known vertices).  Exact solves
+    by sparse LU.  Gradient in V (t held fixed), in t, and in b."""
+    import scipy.sparse.linalg as spla
+    n = np.asarray(V).shape[0]
+    known = np.asarray(known, dtype=bool)
+    u = np.flatnonzero(~known)
+    A = system_matrix(V, F, t).tocsr()[u][:, u].tocsc()
+    m = lumped_mass(V, F)[u]
+    b = np.zeros(u.size)
+    b[s] = m[s]
+    lu = spla.splu(A)
+    x = lu.solve(b)
+    lam = lu.solve(2.0 * m * x)
+    w = x * x
+    w[s] += lam[s]                 # dl/dm through l = sum m x^2 and through b_s = m_s
+    Gop, dt = operator_grad(V, F, t, lam, x, u)
+    dV = mass_grad(V, F, w, u) - Gop
+    return HeatLossResult(loss=float(m @ (x * x)), x=x, lam=lam, dV=dV, dt=-dt, db=lam)
+
+
+def heat_loss(V, F, t, known, s):
+    """The loss of heat_loss_grad alone (for finite differences)."""
+    import scipy.sparse.linalg as spla
+    known = np.asarray(known, dtype=bool)
+    u = np.flatnonzero(~known)
+    A = system_matrix(V, F, t).tocsr()[u][:, u].tocsc()
+    m = lumped_mass(V, F)[u]
+    b = np.zeros(u.size)
+    b[s] = m[s]
+    x = spla.splu(A).solve(b)
+    return float(m @ (x * x))

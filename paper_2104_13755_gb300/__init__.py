@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Plan", "Hierarchy", "Batch", "SmgError", "Options", "Info", "FP64", "MIXED", "lib", "library_path"]
+__all__ = ["Plan", "Hierarchy", "Batch", "differentiable_solve", "differentiable_mass", "SmgError", "Options", "Info", "FP64", "MIXED", "lib", "library_path"]
 
 FP64, MIXED = 0, 1
 
@@ -89,6 +89,9 @@ def _load():
         "smg_cycle_config": (I32, [P, P]),
         "smg_device_bytes": (I64, [P]),
         "smg_residual_norms_noalloc": (I32, [I64, P, P, P, P, P, I32, P, P]),
+        "smg_operator_grad": (I32, [P, P, D, P, P, I32, P, P, P]),
+        "smg_lumped_mass": (I32, [P, P, P, P]),
+        "smg_mass_grad": (I32, [P, P, P, P, P]),
         "smg_batch_create": (I32, [P, I32, P]),
         "smg_batch_destroy": (None, [P]),
         "smg_batch_offsets": (I32, [P, P, P]),
@@ -336,6 +339,29 @@ class Hierarchy:
         _check(lib.smg_apply_mass(self._h, _dev_ptr(x), _dev_ptr(y), nrhs, _stream_ptr(stream)), "smg_apply_mass")
         return y
 
+    def operator_grad(self, V, t, lam, x, stream=None):
+        """(-d/dV lam^T A(V,t) x  as n x 3,  -lam^T L x  as a 1-element tensor)."""
+        import torch
+        gV = torch.empty_like(V)
+        dt = torch.empty(1, dtype=torch.float64, device=V.device)
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        _check(lib.smg_operator_grad(self._h, _dev_ptr(V), float(t), _dev_ptr(lam), _dev_ptr(x), nrhs, _dev_ptr(gV),
+                                     _dev_ptr(dt), _stream_ptr(stream)), "smg_operator_grad")
+        return gV, dt
+
+    def lumped_mass(self, V, stream=None):
+        import torch
+        m = torch.empty(self.n_unknowns, dtype=torch.float64, device=V.device)
+        _check(lib.smg_lumped_mass(self._h, _dev_ptr(V), _dev_ptr(m), _stream_ptr(stream)), "smg_lumped_mass")
+        return m
+
+    def mass_grad(self, V, w, stream=None):
+        import torch
+        gV = torch.empty_like(V)
+        _check(lib.smg_mass_grad(self._h, _dev_ptr(V), _dev_ptr(w), _dev_ptr(gV), _stream_ptr(stream)),
+               "smg_mass_grad")
+        return gV
+
     def level_matrix(self, level, stream=None):
         """Values of A_level aligned with plan.pattern(level)."""
         nnz = self.plan.level_info(level)[1]
@@ -409,3 +435,62 @@ class Batch:
         if check and st != 0:
             _check(st, "smg_batch_solve")
         return x, [i.as_dict() for i in infos]
+
+
+def _autograd():
+    import torch
+
+    class SolveFn(torch.autograd.Function):
+        """x = A(V, t)^{-1} b through the hierarchy; backward runs the adjoint solve
+        lambda = A^{-1} dl/dx with the same hierarchy (A is symmetric) and the
+        per-face derivative kernels for V and t."""
+
+        @staticmethod
+        def forward(ctx, V, t, b, h):
+            tv = float(t)
+            h.update_positions(V.detach().contiguous(), tv)
+            x, _ = h.solve(b.detach().contiguous())
+            ctx.h, ctx.t = h, tv
+            ctx.save_for_backward(V, x)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            V, x = ctx.saved_tensors
+            h = ctx.h
+            Vc = V.detach().contiguous()
+            h.update_positions(Vc, ctx.t)  # the operator of this forward pass
+            lam, _ = h.solve(gx.detach().contiguous())
+            gV, dt = h.operator_grad(Vc, ctx.t, lam, x)
+            return gV, dt.reshape(()), lam, None
+
+    class MassFn(torch.autograd.Function):
+        """Lumped mass diagonal of the unknowns as a function of the positions."""
+
+        @staticmethod
+        def forward(ctx, V, h):
+            ctx.h = h
+            ctx.save_for_backward(V)
+            return h.lumped_mass(V.detach().contiguous())
+
+        @staticmethod
+        def backward(ctx, gm):
+            (V,) = ctx.saved_tensors
+            return ctx.h.mass_grad(V.detach().contiguous(), gm.detach().contiguous()), None
+
+    return SolveFn, MassFn
+
+
+def differentiable_solve(h, V, t, b):
+    """x = A(V, t)^{-1} b, differentiable in V (n x 3), t (0-d tensor) and b."""
+    import torch
+    SolveFn, _ = _autograd()
+    if not torch.is_tensor(t):
+        t = torch.tensor(float(t), dtype=torch.float64, device=V.device)
+    return SolveFn.apply(V, t, b, h)
+
+
+def differentiable_mass(h, V):
+    """Lumped mass diagonal (unknowns) of positions V, differentiable in V."""
+    _, MassFn = _autograd()
+    return MassFn.apply(V, h)

@@ -10,6 +10,7 @@
 #include <stdexcept>
 #include <string>
 
+#include "adjoint.cuh"
 #include "tail.cuh"
 
 using namespace smg;
@@ -680,6 +681,9 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
     ck(cudaMemset(h->Lflat0, 0, sizeof(double) * P.L[0].nflat), "memset");
     h->Mdiag = dalloc<double>(h, P.L[0].n);
     h->perm0 = upload(h, P.L[0].perm);
+    h->vinc_ptr = upload(h, A.vinc_ptr);
+    h->vinc_code = upload(h, A.vinc_code);
+    h->vert_unk = upload(h, A.vert_unk);
     h->state = dalloc<SolveState>(h, 1);
     ck(cudaMemset(h->state, 0, sizeof(SolveState)), "memset");
     h->partials = dalloc<double>(h, (int64_t)kern::kNormBlocks * 2 * kMaxRhs);
@@ -1189,6 +1193,61 @@ int smg_batch_solve(smg_batch* B, const double* b, double* x, int nrhs, smg_info
         if (worst == SMG_OK && st != SMG_OK) worst = st;
     }
     if (worst != SMG_OK) return fail("a mesh of the batch did not converge or was not SPD", worst);
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_lumped_mass(smg_hierarchy* h, const double* V, double* m, smg_stream stream) {
+    if (!h || !V || !m) return fail("null argument", SMG_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    kern::face_geom<<<blocks_for(h->nf), kern::kThreads, 0, s>>>(h->nf, h->F, V, h->facegeom);
+    kern::mass_from_faces<<<blocks_for(h->nv), kern::kThreads, 0, s>>>(h->nv, h->vinc_ptr, h->vinc_code, h->vert_unk,
+                                                                       h->facegeom, m);
+    ck(cudaGetLastError(), "mass");
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+static void ensure_face_scratch(smg_hierarchy* h) {
+    if (!h->facegrad) {
+        h->facegrad = dalloc<double>(h, 9 * h->nf);
+        h->dt_face = dalloc<double>(h, h->nf);
+    }
+}
+
+int smg_mass_grad(smg_hierarchy* h, const double* V, const double* w, double* gradV, smg_stream stream) {
+    if (!h || !V || !w || !gradV) return fail("null argument", SMG_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    ensure_face_scratch(h);
+    kern::face_grad<1><<<blocks_for(h->nf), kern::kThreads, 0, s>>>(h->nf, h->F, V, h->vert_unk, nullptr, nullptr, w,
+                                                                   1, 0.0, 1.0, h->facegrad, h->dt_face);
+    kern::vertex_gather<<<blocks_for(h->nv), kern::kThreads, 0, s>>>(h->nv, h->vinc_ptr, h->vinc_code, h->facegrad,
+                                                                     gradV);
+    ck(cudaGetLastError(), "mass grad");
+    return SMG_OK;
+    SMG_GUARD_END
+}
+
+int smg_operator_grad(smg_hierarchy* h, const double* V, double t, const double* lam, const double* x, int nrhs,
+                      double* gradV, double* dt, smg_stream stream) {
+    if (!h || !V || !lam || !x || !gradV) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (nrhs < 1 || nrhs > kMaxRhs) return fail("nrhs must be 1..4", SMG_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    SMG_GUARD_BEGIN
+    ensure_face_scratch(h);
+    const dim3 grid(blocks_for(h->nf)), block(kern::kThreads);
+    switch (nrhs) {
+        case 1: kern::face_grad<1><<<grid, block, 0, s>>>(h->nf, h->F, V, h->vert_unk, lam, x, nullptr, 0, t, -1.0, h->facegrad, h->dt_face); break;
+        case 2: kern::face_grad<2><<<grid, block, 0, s>>>(h->nf, h->F, V, h->vert_unk, lam, x, nullptr, 0, t, -1.0, h->facegrad, h->dt_face); break;
+        case 3: kern::face_grad<3><<<grid, block, 0, s>>>(h->nf, h->F, V, h->vert_unk, lam, x, nullptr, 0, t, -1.0, h->facegrad, h->dt_face); break;
+        default: kern::face_grad<4><<<grid, block, 0, s>>>(h->nf, h->F, V, h->vert_unk, lam, x, nullptr, 0, t, -1.0, h->facegrad, h->dt_face); break;
+    }
+    kern::vertex_gather<<<blocks_for(h->nv), kern::kThreads, 0, s>>>(h->nv, h->vinc_ptr, h->vinc_code, h->facegrad,
+                                                                     gradV);
+    if (dt) kern::sum_fixed<<<1, kern::kThreads, 0, s>>>(h->nf, h->dt_face, dt);
+    ck(cudaGetLastError(), "operator grad");
     return SMG_OK;
     SMG_GUARD_END
 }

@@ -82,6 +82,11 @@ struct smg_hierarchy {
     double* Lflat0 = nullptr;  // t-independent cotan values on the level-0 flat layout
     double* Mdiag = nullptr;   // lumped mass, permuted level-0 rows
     int32_t* perm0 = nullptr;  // permuted level-0 row -> unknown index
+    int32_t* vinc_ptr = nullptr;   // all vertices: incident face corners
+    int32_t* vinc_code = nullptr;
+    int32_t* vert_unk = nullptr;   // vertex -> unknown index (-1 known)
+    double* facegrad = nullptr;    // 9 per face, allocated by the first derivative call
+    double* dt_face = nullptr;
     bool have_positions = false, have_matrix = false;
     // solve state
     smg::SolveState* state = nullptr;

@@ -512,6 +512,9 @@ int finalize_plan(Plan& p, std::string& err) {
         std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
         for (int64_t f = 0; f < A.nf; f++)
             for (int c = 0; c < 3; c++) vc[fill[A.F[3 * f + c]]++] = (int32_t)(3 * f + c);
+        A.vinc_ptr.assign(cnt.begin(), cnt.end());
+        A.vinc_code = vc;
+        A.vert_unk = unk_of;
         A.inc_ptr.assign(l0.n + 1, 0);
         A.inc_code.clear();
         for (int64_t pr = 0; pr < l0.n; pr++) {

@@ -70,6 +70,8 @@ struct AssemblyPlan {
     std::vector<int32_t> inc_code;     // face * 3 + corner of the row's vertex
     std::vector<int32_t> opp0, opp1;   // per slot: face * 3 + corner opposite the edge (-1 none)
     std::vector<int64_t> flat_to_user; // flat index -> user CSR position (-1 padding)
+    // every mesh vertex: incident face corners, and its unknown index (-1 if known)
+    std::vector<int32_t> vinc_ptr, vinc_code, vert_unk;
 };
 
 struct Plan {
