@@ -116,16 +116,57 @@ void rec_residual(DLevel& L, const LevelView<T>& v, cudaStream_t s) {
                                     x, v.r), "residual launch"));
 }
 
+// Shared-memory slots of the cluster tail: per level, the replica of x (n
+// rounded up to 32) and the distributed b and r (nloc = 32 * ceil(n / (32 CS))
+// rows per CTA), levels packed from the coarsest tail level upwards so a tail
+// that starts at level t needs the first tail_slots(t) slots (times K
+// right-hand sides and the value size), placed after the tail levels' slice
+// tables and staged entries.
+int tail_nloc(int64_t n, int cs) { return (int)((n + 32 * cs - 1) / (32 * cs)) * 32; }
+int tail_npad(int64_t n) { return (int)((n + 31) / 32) * 32; }
+int tail_nwork(const DLevel& L) {
+    int m = 0;
+    for (const auto& en : L.t_E_nmy) m = std::max(m, en.second);
+    return 32 * m;
+}
+int64_t tail_slots(const smg_hierarchy* h, int t) {
+    int64_t slots = 0;
+    for (int l = t; l < h->H; l++)
+        slots += tail_npad(h->L[l].n) + 2 * (int64_t)tail_nloc(h->L[l].n, h->tail_cluster) + tail_nwork(h->L[l]);
+    return slots;
+}
+constexpr size_t kTailSmemMax = 226 * 1024;  // 227 KB per block, less room for the static mbarrier
+
+size_t tail_bytes(const smg_hierarchy* h, int t, bool single, int K) {
+    const std::vector<int>& db = single ? h->tail_dbase32 : h->tail_dbase64;
+    return (size_t)db[t] + (size_t)tail_slots(h, t) * K * (single ? sizeof(float) : sizeof(double));
+}
+
+// First tail level for K right-hand sides: the tuned level, moved down while its
+// shared memory does not fit in one CTA.
+int tail_start(const smg_hierarchy* h, bool single, int K) {
+    if (h->tail_cluster == 0 || h->H == 0) return h->H;
+    int t = std::min(single ? h->tail32 : h->tail64, h->H);
+    while (t < h->H && tail_bytes(h, t, single, K) > kTailSmemMax) t++;
+    return t;
+}
+
 template <typename T, int K>
 void rec_tail(smg_hierarchy* h, bool down, int t, cudaStream_t s) {
     const bool single = sizeof(T) == 4;
-    const TailLevel<T>* lv = (const TailLevel<T>*)(single ? h->tail_lv32 : h->tail_lv64);
+    const TailLevel<T>* lv = (const TailLevel<T>*)(single ? h->tail_lv32 : h->tail_lv64) + (size_t)t * h->H;
     const dim3 block(kern::kTailThreads);
-    if (down) ck(launch_cluster_pdl(kern::tail_down<T, K>, h->tail_cluster, block, s, lv, t, h->H, h->opts.mu_pre),
-                 "tail down");
-    else ck(launch_cluster_pdl(kern::tail_up<T, K>, h->tail_cluster, block, s, lv, t, h->H, h->opts.mu_post,
-                               h->opts.post_reverse != 0 ? 1 : 0),
-            "tail up");
+    const size_t smem = tail_bytes(h, t, single, K);
+    const int lg = h->tail_cluster == 16 ? 4 : 3;
+    const int dbase = (single ? h->tail_dbase32 : h->tail_dbase64)[t];
+    if (down)
+        ck(launch_cluster_pdl(kern::tail_down<T, K>, h->tail_cluster, block, smem, s, lv, t, h->H, h->opts.mu_pre, lg,
+                              dbase),
+           "tail down");
+    else
+        ck(launch_cluster_pdl(kern::tail_up<T, K>, h->tail_cluster, block, smem, s, lv, t, h->H, h->opts.mu_post,
+                              h->opts.post_reverse != 0 ? 1 : 0, lg, dbase),
+           "tail up");
 }
 
 // One V-cycle of Alg. 2 on the level buffers (x_0, b_0 of the chosen precision).
@@ -135,7 +176,7 @@ template <typename T, int K>
 void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
     const int H = h->H;
     const bool single = sizeof(T) == 4;
-    const int t = std::min(single ? h->tail32 : h->tail64, H);
+    const int t = tail_start(h, single, K);
     for (int l = 0; l < t; l++) {
         DLevel& L = h->L[l];
         DLevel& N = h->L[l + 1];
@@ -408,57 +449,146 @@ void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
     }
 }
 
-template <typename T>
-std::vector<TailLevel<T>> tail_table(smg_hierarchy* h) {
-    std::vector<TailLevel<T>> tab(h->H);
+// Per-CTA slice tables of every level for a cluster of cs CTAs (layout in
+// TailLevel): CTA r takes the slices of each colour class whose first row lies
+// in one of its 32-row blocks.
+void build_tail_tables(smg_hierarchy* h, const Plan& P, int cs) {
     for (int l = 0; l < h->H; l++) {
+        const LevelPlan& lp = P.L[l];
+        DLevel& L = h->L[l];
+        const int nc = (int)lp.colour_slice.size() - 1;
+        std::vector<int32_t> tab, off(cs + 1, 0);
+        L.t_E_nmy.assign(cs, {0, 0});
+        L.ttab_ints = 0;
+        for (int r = 0; r < cs; r++) {
+            off[r] = (int32_t)tab.size();
+            const size_t head = tab.size();
+            tab.push_back(0);
+            tab.push_back(0);
+            std::vector<int32_t> cfirst(nc + 1, 0), ent;
+            int n_my = 0, E = 0;
+            for (int c = 0; c < nc; c++) {
+                cfirst[c] = n_my;
+                const int s0 = lp.colour_slice[c], s1 = lp.colour_slice[c + 1];
+                const int owner0 = (lp.colour_row[c] >> 5) & (cs - 1);
+                const int first = (r - owner0) & (cs - 1);
+                for (int s = s0 + first; s < s1; s += cs) {
+                    const SliceMeta& m = lp.slices[s];
+                    ent.insert(ent.end(), {(int32_t)m.off, m.width, m.row0, m.nrows, E});
+                    E += m.width * 32;
+                    n_my++;
+                }
+            }
+            cfirst[nc] = n_my;
+            tab[head] = n_my;
+            tab[head + 1] = E;
+            tab.insert(tab.end(), cfirst.begin(), cfirst.end());
+            for (int c = 0; c < nc; c++) tab.push_back(lp.colour_row[c + 1] - lp.colour_row[c]);
+            tab.insert(tab.end(), ent.begin(), ent.end());
+            L.t_E_nmy[r] = {E, n_my};
+            L.ttab_ints = std::max(L.ttab_ints, (int)(tab.size() - head));
+        }
+        off[cs] = (int32_t)tab.size();
+        L.ttab = upload(h, tab);
+        L.ttab_off = upload(h, off);
+    }
+}
+
+// Tail views of every level for one precision and a tail that starts at level
+// t, with its shared-memory regions: levels packed from the coarsest upwards,
+// each with its slice table and, while the staged copies still fit next to the
+// arrays of one right-hand side, its staged entries (coarsest levels first).
+// Returns H views; dbase = bytes of the regions of levels t..H-1.
+template <typename T>
+std::vector<TailLevel<T>> tail_table(smg_hierarchy* h, int t, int& dbase) {
+    std::vector<TailLevel<T>> tab(h->H);
+    const int cs = std::max(h->tail_cluster, 8);
+    int64_t budget = (int64_t)kTailSmemMax - (h->tail_cluster ? tail_slots(h, t) * (int64_t)sizeof(T) : 0);
+    for (int l = t; l < h->H; l++) budget -= ((h->L[l].ttab_ints * 4 + 15) / 16) * 16;
+    int64_t sbase = 0, rbase = 0;
+    for (int l = h->H - 1; l >= 0; l--) {
         DLevel& L = h->L[l];
         DLevel& N = h->L[l + 1];
         LevelView<T> v = view<T>(L);
         LevelView<T> vn = view<T>(N);
-        TailLevel<T>& t = tab[l];
-        t.slices = L.slices;
-        t.col = L.sell_col;
-        t.sval = v.sval;
-        t.dinv = v.dinv;
-        t.diag = v.diag;
-        t.colour_slice = L.colour_slice_dev;
-        t.x = v.x;
-        t.b = v.b;
-        t.r = v.r;
-        t.nslices = L.nslices;
-        t.ncolours = L.ncolours;
-        t.n = (int)L.n;
-        t.pt_ptr = L.pt_ptr;
-        t.pt_row = L.pt_row;
-        t.pt_w = v.pt_w;
-        t.n_next = (int)N.n;
-        t.b_next = vn.b;
-        t.x_next = vn.x;
-        t.p_idx = L.p_idx;
-        t.p_w = v.p_w;
+        TailLevel<T>& e = tab[l];
+        e.slices = L.slices;
+        e.col = L.sell_col;
+        e.sval = v.sval;
+        e.dinv = v.dinv;
+        e.diag = v.diag;
+        e.colour_row = L.colour_row_dev;
+        e.table = L.ttab;
+        e.table_off = L.ttab_off;
+        e.x = v.x;
+        e.b = v.b;
+        e.nslices = L.nslices;
+        e.ncolours = L.ncolours;
+        e.n = (int)L.n;
+        e.rlg = L.maxw <= 32 ? 3 : L.maxw <= 64 ? 4 : 5;  // 4 entries per lane in registers
+        e.nloc = tail_nloc(L.n, cs);
+        e.npad = tail_npad(L.n);
+        e.nwork = tail_nwork(L);
+        e.sbase = (int)sbase;
+        sbase += e.npad + 2 * (int64_t)e.nloc + e.nwork;
+        int stage = 0;
+        for (const auto& en : L.t_E_nmy) stage = std::max(stage, StageLayout<T>(en.first, en.second).bytes);
+        e.tbytes = ((L.ttab_ints * 4 + 15) / 16) * 16;
+        e.staged = (l >= t && stage <= budget) ? 1 : 0;
+        if (e.staged) budget -= stage;
+        e.rbase = (int)rbase;
+        if (l >= t) rbase += e.tbytes + (e.staged ? stage : 0);
+        e.pt_ptr = L.pt_ptr;
+        e.pt_row = L.pt_row;
+        e.pt_w = v.pt_w;
+        e.n_next = (int)N.n;
+        e.b_next = vn.b;
+        e.x_next = vn.x;
+        e.p_idx = L.p_idx;
+        e.p_w = v.p_w;
+        e.err = &h->state->tail_err;
     }
+    dbase = (int)rbase;
     return tab;
 }
 
+// Views for every tail start, uploaded as one [t][l] array per precision.
+template <typename T>
+void* upload_tail_tables(smg_hierarchy* h, std::vector<int>& dbase) {
+    const int H = h->H;
+    dbase.assign(H + 1, 0);
+    std::vector<TailLevel<T>> all;
+    all.reserve((size_t)H * H);
+    for (int t = 0; t < H; t++) {
+        std::vector<TailLevel<T>> tab = tail_table<T>(h, t, dbase[t]);
+        all.insert(all.end(), tab.begin(), tab.end());
+    }
+    TailLevel<T>* d = dalloc<TailLevel<T>>(h, (int64_t)H * H);
+    ck(cudaMemcpy(d, all.data(), sizeof(TailLevel<T>) * all.size(), cudaMemcpyHostToDevice), "upload");
+    return d;
+}
+
 template <typename T, int K>
-void allow_wide_clusters() {
-    cudaFuncSetAttribute(kern::tail_down<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(kern::tail_up<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+bool allow_wide_clusters() {
+    bool ok = cudaFuncSetAttribute(kern::tail_down<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+              cudaSuccess;
+    ok &= cudaFuncSetAttribute(kern::tail_up<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(kern::tail_down<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTailSmemMax) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(kern::tail_up<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax) ==
+          cudaSuccess;
+    return ok;
 }
 
 // CTAs per tail cluster: 16 (non-portable) when the device can schedule it, else
 // the portable 8, else 0 (no tail).
 int detect_tail_cluster() {
-    allow_wide_clusters<double, 1>();
-    allow_wide_clusters<double, 2>();
-    allow_wide_clusters<double, 3>();
-    allow_wide_clusters<double, 4>();
-    allow_wide_clusters<float, 1>();
-    allow_wide_clusters<float, 2>();
-    allow_wide_clusters<float, 3>();
-    allow_wide_clusters<float, 4>();
+    bool ok = allow_wide_clusters<double, 1>() && allow_wide_clusters<double, 2>() &&
+              allow_wide_clusters<double, 3>() && allow_wide_clusters<double, 4>() &&
+              allow_wide_clusters<float, 1>() && allow_wide_clusters<float, 2>() && allow_wide_clusters<float, 3>() &&
+              allow_wide_clusters<float, 4>();
     cudaGetLastError();
+    if (!ok) return 0;  // the tail kernels cannot get their shared memory: no tail
     for (int cs : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs);
@@ -647,6 +777,8 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
         L.slices = upload(h, lp.slices);
         L.sell_col = upload(h, lp.sell_col);
         L.colour_slice_dev = upload(h, lp.colour_slice);
+        L.colour_row_dev = upload(h, lp.colour_row);
+        for (const SliceMeta& m : lp.slices) L.maxw = std::max(L.maxw, (int)m.width);
         L.dinv = dalloc<double>(h, L.n);
         L.vals32 = dalloc<float>(h, L.nflat);
         L.dinv32 = dalloc<float>(h, L.n);
@@ -688,15 +820,12 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
     ck(cudaMemset(h->state, 0, sizeof(SolveState)), "memset");
     h->partials = dalloc<double>(h, (int64_t)kern::kNormBlocks * 2 * kMaxRhs);
     ck(cudaMallocHost((void**)&h->state_host, sizeof(SolveState)), "cudaMallocHost");
-    if (h->H > 0) {
-        std::vector<TailLevel<double>> t64 = tail_table<double>(h);
-        std::vector<TailLevel<float>> t32 = tail_table<float>(h);
-        h->tail_lv64 = dalloc<TailLevel<double>>(h, h->H);
-        h->tail_lv32 = dalloc<TailLevel<float>>(h, h->H);
-        ck(cudaMemcpy(h->tail_lv64, t64.data(), sizeof(TailLevel<double>) * h->H, cudaMemcpyHostToDevice), "upload");
-        ck(cudaMemcpy(h->tail_lv32, t32.data(), sizeof(TailLevel<float>) * h->H, cudaMemcpyHostToDevice), "upload");
-    }
     h->tail_cluster = detect_tail_cluster();
+    if (h->H > 0) {
+        build_tail_tables(h, P, std::max(h->tail_cluster, 8));
+        h->tail_lv64 = upload_tail_tables<double>(h, h->tail_dbase64);
+        h->tail_lv32 = upload_tail_tables<float>(h, h->tail_dbase32);
+    }
     ck(cudaDeviceSynchronize(), "upload");
     choose_lanes(h, P, o.autotune != 0);
     choose_tail(h, o.autotune != 0);
@@ -939,6 +1068,7 @@ int smg_solve_result(smg_hierarchy* h, smg_info* info) {
         info->rho = (ss.cycles > 0 && ss.rel0 > 0) ? std::pow(ss.rel / ss.rel0, 1.0 / ss.cycles) : 0.0;
     }
     if (ss.chol_bad) return fail("coarsest operator is not positive definite", SMG_ERR_NOT_SPD);
+    if (ss.tail_err) return fail("cluster tail: wait for staged matrix entries timed out", SMG_ERR_CUDA);
     if (ss.status == SMG_ERR_NOT_CONVERGED) return fail("not converged within max_cycles", ss.status);
     if (ss.status == SMG_ERR_DIVERGED) return fail("residual became non-finite", ss.status);
     return SMG_OK;

@@ -23,7 +23,7 @@ struct SolveState {
     int32_t cycles;
     int32_t status;          // SMG_OK / SMG_ERR_NOT_CONVERGED / SMG_ERR_DIVERGED / -1 running
     int32_t chol_bad;        // nonzero: a coarsest pivot was not positive
-    int32_t pad;
+    int32_t tail_err;        // nonzero: a cluster-tail wait for staged matrix entries timed out
 };
 
 struct DLevel {
@@ -33,7 +33,14 @@ struct DLevel {
     int R = 1;    // lanes per row of the binary64 kernels
     int R32 = 1;  // lanes per row of the binary32 kernels
     int32_t* colour_slice_dev = nullptr;
+    int32_t* colour_row_dev = nullptr;
+    int maxw = 0;  // widest slice (off-diagonal entries per row)
     std::vector<int32_t> colour_slice;  // host copy, ncolours + 1
+    // cluster tail: per-CTA slice tables (see TailLevel) and their sizes
+    int32_t* ttab = nullptr;
+    int32_t* ttab_off = nullptr;
+    int ttab_ints = 0;                      // largest per-CTA table
+    std::vector<std::pair<int, int>> t_E_nmy;  // per CTA: staged entries, slices
     SliceMeta* slices = nullptr;
     int32_t* sell_col = nullptr;
     double* vals = nullptr;  // flat A_l
@@ -106,6 +113,7 @@ struct smg_hierarchy {
     void* tail_lv64 = nullptr;  // TailLevel<double>[H]
     void* tail_lv32 = nullptr;  // TailLevel<float>[H]
     int tail64 = 0, tail32 = 0;  // first tail level per precision (H = no tail)
+    std::vector<int> tail_dbase64, tail_dbase32;  // per first tail level: bytes of tables + staged entries
     int tail_cluster = 0;        // CTAs per tail cluster (0 = clusters unavailable)
 };
 
@@ -138,12 +146,12 @@ void record_coarsest_solve(smg_hierarchy* h, int K, const void* in, bool in32, v
 // Cluster launch (grid = one cluster of `cluster` CTAs) with programmatic stream
 // serialization; the kernel must call griddepcontrol.wait before dependent reads.
 template <typename... Params, typename... Args>
-inline cudaError_t launch_cluster_pdl(void (*kernel)(Params...), int cluster, dim3 block, cudaStream_t s,
-                                      Args&&... args) {
+inline cudaError_t launch_cluster_pdl(void (*kernel)(Params...), int cluster, dim3 block, size_t smem,
+                                      cudaStream_t s, Args&&... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cluster);
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;

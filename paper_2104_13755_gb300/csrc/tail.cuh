@@ -1,12 +1,23 @@
 // Cluster tail of the V-cycle: the levels below a tuned size run inside one
-// thread-block cluster (up to 16 CTAs, one per SM), one launch for the whole
-// down-sweep (pre-relaxation, residual, restriction of every tail level) and one
-// for the up-sweep (prolongation with correction, post-relaxation).  Colour
-// classes and level transfers are separated by the cluster barrier (release /
-// acquire at cluster scope) instead of kernel boundaries; values written inside
-// the launch are read through L2 (ld.global.cg).  The arithmetic per row is the
-// same as the full-GPU kernels (Alg. 2 with the multicolour Gauss-Seidel of
-// App. "Multi-Color Gauss Seidel").
+// thread-block cluster (16 CTAs, one per SM; 8 where 16 cannot be scheduled),
+// one launch for the whole down-sweep (pre-relaxation, residual, restriction of
+// every tail level) and one for the up-sweep (prolongation with correction,
+// post-relaxation).  The arithmetic per row is that of the full-GPU kernels
+// (Alg. 2 with the multicolour Gauss-Seidel of App. "Multi-Color Gauss Seidel").
+//
+// Every CTA keeps a full replica of each tail level's iterate x in its shared
+// memory, so the gathers of a colour step are local shared-memory loads; a
+// row's new value is written into all replicas (st.shared::cluster, spread over
+// the row's lanes) and colour classes are separated by the cluster barrier.
+// Remote shared-memory loads are an order of magnitude slower than local ones
+// in throughput, which is why x is replicated rather than distributed.  The
+// right-hand side b and the residual r are distributed: row i belongs to CTA
+// (i / 32) mod CS at local slot (i / (32 CS)) * 32 + i mod 32.  Each warp loads
+// the matrix entries, diagonal and right-hand side of its next colour step
+// between the arrive and the wait of the barrier ahead of it; where they fit,
+// a CTA's matrix entries are staged in shared memory at kernel entry.  Global
+// copies of x and b are read at entry and written at exit (the coarsest solve
+// and the full-GPU levels run between the two launches).
 #pragma once
 
 #include "kernels.cuh"
@@ -14,6 +25,17 @@
 namespace smg {
 
 // Device view of one level for the tail kernels (one precision).
+//
+// Each CTA works on the slices whose first row lies in one of its 32-row blocks
+// (a class's slices start 32 rows apart, so they rotate over the CTAs).  The
+// host writes, per CTA, a table of those slices, which the kernels copy to
+// shared memory at entry:
+//   [n_my, E] [cfirst: ncolours + 1] [rows: ncolours] [n_my x {off, W, row0, nrows, soff}]
+// (cfirst[c] = index of the CTA's first slice of colour c, rows[c] = rows of colour c
+// in the level, E = sum W * 32, soff =
+// the slice's first entry in the staged copy).  When the level is staged, the
+// CTA also copies its slices' column indices, values, reciprocal diagonal and
+// diagonal to shared memory, so a colour step touches global memory not at all.
 template <typename T>
 struct TailLevel {
     const SliceMeta* slices;
@@ -21,111 +43,531 @@ struct TailLevel {
     const T* sval;
     const T* dinv;
     const T* diag;
-    const int32_t* colour_slice;  // ncolours + 1 slice offsets
-    T* x;
+    const int32_t* colour_row;    // ncolours + 1 row offsets
+    const int32_t* table;         // per-CTA slice tables, concatenated
+    const int32_t* table_off;     // CS + 1 offsets into table
+    T* x;                         // global copies (entry and exit)
     T* b;
-    T* r;
     int nslices, ncolours, n;
+    int rlg;                      // log2 of the lanes per row (8, 16 or 32: 4 entries per lane cover the longest row)
+    int nloc;                     // distributed slots per CTA (multiple of 32)
+    int npad;                     // replica slots of x (n rounded up to 32)
+    int nwork;                    // slots of the local copy of b for this CTA's rows (32 per slice, max over CTAs)
+    int sbase;                    // first slot of this level's arrays: x replica at sbase, b at +npad, r at
+                                  // +npad+nloc, local b at +npad+2 nloc
+    int staged;                   // matrix entries copied to shared memory
+    int rbase;                    // byte offset of this level's table (and staged entries) in shared memory
+    int tbytes;                   // bytes reserved for the table (maximum over CTAs, multiple of 16)
     // restriction into level + 1
     const int32_t* pt_ptr;
     const int32_t* pt_row;
     const T* pt_w;
     int n_next;
-    T* b_next;
+    T* b_next;                    // global arrays of level + 1 (used when it is outside the tail)
     T* x_next;
+    int* err;                     // set when a wait for staged entries times out
     // prolongation from level + 1
     const int32_t* p_idx;
     const T* p_w;
 };
 
+// Byte layout of a staged copy of E entries over n_my slices (value type T).
+template <typename T>
+struct StageLayout {
+    int col, val, dinv, diag, bytes;
+    __host__ __device__ StageLayout(int E, int n_my) {
+        col = 0;
+        val = ((E * 4 + 15) / 16) * 16;
+        dinv = val + ((E * (int)sizeof(T) + 15) / 16) * 16;
+        diag = dinv + ((n_my * 32 * (int)sizeof(T) + 15) / 16) * 16;
+        bytes = diag + ((n_my * 32 * (int)sizeof(T) + 15) / 16) * 16;
+    }
+};
+
 namespace kern {
 
 constexpr int kTailThreads = 512;
-constexpr int kTailR = 8;  // lanes per row inside the tail
+constexpr int kTailWarps = kTailThreads / 32;
+constexpr int kTailPre = 4;  // entries per lane held in registers
 
-// Cluster-wide barrier with release / acquire ordering of memory at cluster
-// scope.  The non-.aligned form: a warp may reach it after divergent loops.
+// Split cluster barrier.  The release at arrive covers this thread's earlier
+// stores; loads of data that the phase does not write (matrix entries, b) may
+// be issued between arrive and wait, so their latency overlaps the barrier.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 __device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+    cluster_arrive();
+    cluster_wait();
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cta address -> shared::cluster address of the same offset in CTA `rank`
+__device__ __forceinline__ uint32_t dsm(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double ldc(uint32_t a, double*) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float ldc(uint32_t a, float*) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void stc(uint32_t a, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void stc(uint32_t a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ T ldc(uint32_t a) {
+    return ldc(a, (T*)nullptr);
 }
 
-template <typename T, int K>
-__device__ __forceinline__ void tail_gs(const TailLevel<T>& L, int c, int gwarp, int nwarps, int lane) {
-    const int s0 = L.colour_slice[c], s1 = L.colour_slice[c + 1];
-    const int need = (s1 - s0) * kTailR;
-    for (int w = gwarp; w < need; w += nwarps) {
-        const SliceMeta m = L.slices[s0 + w / kTailR];
-        RowSlice<T, K, kTailR, Pre<T, K>::value> rs;
-        rs.load(m, w % kTailR, lane, L.col, L.sval);
-        const bool valid = rs.r < m.nrows;
-        const int row = m.row0 + (valid ? rs.r : 0);
-        const T d = L.dinv[row];
-        T acc[K];
-        rs.template dot<true>(m, L.col, L.sval, L.x, acc);
-        if (valid && rs.sub == 0)
-#pragma unroll
-            for (int q = 0; q < K; q++) L.x[(int64_t)row * K + q] = (__ldcg(L.b + (int64_t)row * K + q) + acc[q]) * d;
+__device__ __forceinline__ unsigned char* tail_smem() {
+    extern __shared__ __align__(16) unsigned char tail_dyn_smem[];
+    return tail_dyn_smem;
+}
+
+__device__ __forceinline__ double lds(uint32_t a, double*) {
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds(uint32_t a, float*) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T lds(uint32_t a) {
+    return lds(a, (T*)nullptr);
+}
+__device__ __forceinline__ void sts(uint32_t a, double v) {
+    asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void sts(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ int lds_i(uint32_t a) {
+    int v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_i(uint32_t a, int v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// Rows over the CS = 1 << lg CTAs of the cluster (distributed arrays) and the
+// local replicas.
+struct Dist {
+    uint32_t base;  // shared::cta address of the per-level arrays
+    int lg;
+    uint32_t rank;
+    __device__ __forceinline__ uint32_t owner(int i) const { return (uint32_t)(i >> 5) & ((1u << lg) - 1u); }
+    __device__ __forceinline__ int local(int i) const { return ((i >> (5 + lg)) << 5) | (i & 31); }
+    __device__ __forceinline__ int global(int li) const {
+        return ((li >> 5) << (5 + lg)) | (int)(rank << 5) | (li & 31);
     }
+    // cluster address of value 0 of distributed row i in the array at slot offset arr
+    template <typename T, int K>
+    __device__ __forceinline__ uint32_t at(int arr, int i) const {
+        return dsm(base + (uint32_t)(((arr + local(i)) * K) * (int)sizeof(T)), owner(i));
+    }
+    // this CTA's own slot li of distributed array arr (cluster address)
+    template <typename T, int K>
+    __device__ __forceinline__ uint32_t own(int arr, int li) const {
+        return dsm(base + (uint32_t)(((arr + li) * K) * (int)sizeof(T)), rank);
+    }
+    // shared::cta address of value 0 of row i in the local replica at slot offset arr
+    template <typename T, int K>
+    __device__ __forceinline__ uint32_t rep(int arr, int i) const {
+        return base + (uint32_t)(((arr + i) * K) * (int)sizeof(T));
+    }
+};
+
+// This CTA's view of one tail level: its slice table (and staged entries) in
+// shared memory, by shared::cta address.
+template <typename T>
+struct LevelCtx {
+    const TailLevel<T>* L;
+    uint32_t tab;  // [n_my, E, cfirst[nc + 1], rows[nc], 5 * n_my]
+    int n_my, nc, rlg, staged;
+    uint32_t scol, sval, sdinv, sdiag;
+    uint32_t bw;  // local copy of b (32 rows per slice)
+    __device__ __forceinline__ int cfirst(int c) const { return lds_i(tab + 4u * (2 + c)); }
+    __device__ __forceinline__ int rows(int c) const { return lds_i(tab + 4u * (3 + nc + c)); }
+    // field f of slice i: 0 off, 1 W, 2 row0, 3 nrows, 4 soff
+    __device__ __forceinline__ int slice(int i, int f) const { return lds_i(tab + 4u * (3 + 2 * nc + 5 * i + f)); }
+};
+
+// mbarrier and bulk-copy helpers (shared::cta addresses).
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Wait for phase `parity` of the mbarrier; gives up after a bounded number of
+// polls (the copies it waits for are a few hundred kilobytes at most) and
+// reports that through *err instead of hanging.
+__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+    if (err && *(volatile int*)err) return;  // an earlier wait gave up: do not wait again
+    for (int it = 0; it < (1 << 22); it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return;
+    }
+    if (err) atomicExch(err, 1);
 }
 
+// A value into shared::cluster address a, counted on the mbarrier at cluster
+// address bar (in the CTA that owns a) as sizeof(value) completed bytes.
+__device__ __forceinline__ void st_async(uint32_t a, double v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(a), "d"(v), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t a, float v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(a), "f"(v), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_local(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.relaxed.cluster.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+// Wait for phase `parity` with acquire at cluster scope; bounded like mbar_wait.
+__device__ __forceinline__ void mbar_wait_cluster(uint32_t bar, uint32_t parity, int* err) {
+    if (err && *(volatile int*)err) return;  // an earlier wait gave up: do not wait again
+    for (int it = 0; it < (1 << 22); it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return;
+    }
+    if (err) atomicExch(err, 1);
+}
+
+// Step barriers of the relaxation: two mbarriers (even and odd steps), each
+// completing when every CTA of the cluster has arrived for the step and the
+// step's new x values (every row of the colour, into this CTA's replica) have
+// landed.  A CTA arrives for step k only after finishing step k - 1, so no CTA
+// runs more than one step ahead of another and two barriers suffice.
+struct StepBars {
+    uint32_t bar0;  // shared::cta address of the even-step mbarrier (the odd one follows)
+    uint32_t step;  // steps taken so far in this launch
+    __device__ __forceinline__ uint32_t bar() const { return bar0 + 8u * (step & 1u); }
+    __device__ __forceinline__ uint32_t parity() const { return (step >> 1) & 1u; }
+};
+
+// Copy this CTA's slice table into shared memory, and its slices' matrix
+// entries too when the level is staged (bulk copies completing on the CTA's
+// mbarrier, one per slice and array); gather b of its slices' rows into the
+// local copy.  CTA-local, ends with __syncthreads.  `phase` counts the uses of
+// the mbarrier.
 template <typename T, int K>
-__device__ __forceinline__ void tail_residual(const TailLevel<T>& L, int gwarp, int nwarps, int lane) {
-    const int need = L.nslices * kTailR;
-    for (int w = gwarp; w < need; w += nwarps) {
-        const SliceMeta m = L.slices[w / kTailR];
-        RowSlice<T, K, kTailR, Pre<T, K>::value> rs;
-        rs.load(m, w % kTailR, lane, L.col, L.sval);
-        const bool valid = rs.r < m.nrows;
-        const int row = m.row0 + (valid ? rs.r : 0);
-        const T d = L.diag[row];
-        T acc[K];
-        rs.template dot<true>(m, L.col, L.sval, L.x, acc);
-        if (valid && rs.sub == 0)
+__device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const Dist& D, uint32_t bar,
+                                                   uint32_t& phase) {
+    const TailLevel<T>& L = *Lp;
+    const uint32_t sm = (uint32_t)__cvta_generic_to_shared(tail_smem()) + (uint32_t)L.rbase;
+    const int t0 = L.table_off[D.rank], t1 = L.table_off[D.rank + 1];
+    for (int e = threadIdx.x; e < t1 - t0; e += kTailThreads) sts_i(sm + 4u * e, L.table[t0 + e]);
+    __syncthreads();
+    LevelCtx<T> C;
+    C.L = Lp;
+    C.tab = sm;
+    C.n_my = lds_i(sm);
+    const int E = lds_i(sm + 4u);
+    C.nc = L.ncolours;
+    C.rlg = L.rlg;
+    C.staged = L.staged;
+    const StageLayout<T> lay(E, C.n_my);
+    const uint32_t st = sm + (uint32_t)L.tbytes;
+    C.scol = st + lay.col;
+    C.sval = st + lay.val;
+    C.sdinv = st + lay.dinv;
+    C.sdiag = st + lay.diag;
+    C.bw = D.template rep<T, K>(L.sbase + L.npad + 2 * L.nloc, 0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (C.staged && E > 0) {
+        if (threadIdx.x == 0) mbar_expect(bar, (uint32_t)E * (uint32_t)(4 + sizeof(T)));
+        __syncthreads();
+        for (int i = threadIdx.x; i < C.n_my; i += kTailThreads) {
+            const int off = C.slice(i, 0), W = C.slice(i, 1), soff = C.slice(i, 4);
+            if (W == 0) continue;  // rows without off-diagonal entries: nothing to copy
+            bulk_g2s(C.scol + 4u * soff, L.col + off, (uint32_t)W * 32u * 4u, bar);
+            bulk_g2s(C.sval + (uint32_t)sizeof(T) * soff, L.sval + off, (uint32_t)W * 32u * (uint32_t)sizeof(T), bar);
+        }
+    }
+    for (int i = warp; i < C.n_my; i += kTailWarps) {
+        const int row0 = C.slice(i, 2), nrows = C.slice(i, 3);
+        if (lane < nrows) {
+            if (C.staged) {
+                sts(C.sdinv + (uint32_t)sizeof(T) * (32 * i + lane), L.dinv[row0 + lane]);
+                sts(C.sdiag + (uint32_t)sizeof(T) * (32 * i + lane), L.diag[row0 + lane]);
+            }
+            const uint32_t src = D.template at<T, K>(L.sbase + L.npad, row0 + lane);
 #pragma unroll
             for (int q = 0; q < K; q++)
-                L.r[(int64_t)row * K + q] =
-                    (__ldcg(L.b + (int64_t)row * K + q) - d * __ldcg(L.x + (int64_t)row * K + q)) + acc[q];
+                sts(C.bw + ((32 * i + lane) * K + q) * (int)sizeof(T), ldc<T>(src + q * (int)sizeof(T)));
+        }
+    }
+    if (C.staged && E > 0) {
+        mbar_wait(bar, phase & 1u, L.err);
+        phase++;
+    }
+    __syncthreads();
+    return C;
+}
+
+// One warp's share of a SELL-32 slice (R = 2^rlg lanes per row, 32 / R rows per
+// warp), loaded ahead of the barrier that precedes its use.
+template <typename T, int K>
+struct TailRows {
+    static constexpr int PRE = kTailPre;
+    uint32_t xa[PRE];  // local replica address of x at each entry's column
+    T v[PRE];
+    T bb[K];
+    T d;
+    uint32_t xrow;     // local replica address of this row's x (GS: offset for the broadcast)
+    uint32_t rself;    // cluster address of this row's r (residual)
+    int base;          // first entry of the slice: staged offset (shared) or SELL offset (global)
+    int W, r, sub, rlg;
+    bool live, valid, staged;
+
+    __device__ __forceinline__ int col_at(const LevelCtx<T>& C, int k) const {
+        const int e = base + k * 32 + r;
+        return staged ? lds_i(C.scol + 4u * e) : __ldg(C.L->col + e);
+    }
+    __device__ __forceinline__ T val_at(const LevelCtx<T>& C, int k) const {
+        const int e = base + k * 32 + r;
+        return staged ? lds<T>(C.sval + (uint32_t)sizeof(T) * e) : __ldg(C.L->sval + e);
+    }
+
+    // my slice i (or none when i < 0), sub-slice g; RESIDUAL: diagonal, else its reciprocal
+    template <bool RESIDUAL>
+    __device__ __forceinline__ void load(const LevelCtx<T>& C, const Dist& D, int i, int g, int lane) {
+        live = i >= 0;
+        if (!live) return;
+        const TailLevel<T>& L = *C.L;
+        staged = C.staged != 0;
+        const int row0 = C.slice(i, 2), nrows = C.slice(i, 3);
+        W = C.slice(i, 1);
+        base = staged ? C.slice(i, 4) : C.slice(i, 0);
+        rlg = C.rlg;
+        const int rl_lg = 5 - rlg;  // log2 rows per warp
+        sub = lane >> rl_lg;
+        r = (g << rl_lg) + (lane & ((1 << rl_lg) - 1));
+        valid = r < nrows;
+        const int row = row0 + (valid ? r : 0);
+#pragma unroll
+        for (int u = 0; u < PRE; u++) {
+            const int k = sub + (u << rlg);
+            if (k < W) {
+                const int c = col_at(C, k);
+                v[u] = val_at(C, k);
+                xa[u] = D.template rep<T, K>(L.sbase, c);
+            }
+        }
+        if (staged) d = lds<T>((RESIDUAL ? C.sdiag : C.sdinv) + (uint32_t)sizeof(T) * (32 * i + r));
+        else d = RESIDUAL ? L.diag[row] : L.dinv[row];
+        const uint32_t ba = C.bw + (uint32_t)(((32 * i + r) * K) * (int)sizeof(T));
+#pragma unroll
+        for (int q = 0; q < K; q++) bb[q] = lds<T>(ba + q * (int)sizeof(T));
+        xrow = D.template rep<T, K>(L.sbase, row);
+        if (RESIDUAL) rself = D.template at<T, K>(L.sbase + L.npad + L.nloc, row);
+    }
+
+    // GS: x_row <- (b_row - sum a x) / a_rr into every replica; residual:
+    // r_row <- b_row - a_rr x_row - sum a x at the owner
+    template <bool RESIDUAL>
+    __device__ __forceinline__ void run(const LevelCtx<T>& C, const Dist& D, uint32_t sbar = 0) const {
+        if (!live) return;  // uniform over the warp
+        T xv[PRE][K];
+#pragma unroll
+        for (int u = 0; u < PRE; u++)
+            if (sub + (u << rlg) < W)
+#pragma unroll
+                for (int q = 0; q < K; q++) xv[u][q] = lds<T>(xa[u] + q * (int)sizeof(T));
+        T a0[K], a1[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) a0[q] = a1[q] = T(0);
+#pragma unroll
+        for (int u = 0; u < PRE; u++)
+            if (sub + (u << rlg) < W)
+#pragma unroll
+                for (int q = 0; q < K; q++) {
+                    if (u & 1) a1[q] -= v[u] * xv[u][q];
+                    else a0[q] -= v[u] * xv[u][q];
+                }
+        for (int k = sub + (PRE << rlg); k < W; k += 1 << rlg) {  // rows longer than PRE * R
+            const int c = col_at(C, k);
+            const T vv = val_at(C, k);
+            const uint32_t a = D.template rep<T, K>(C.L->sbase, c);
+#pragma unroll
+            for (int q = 0; q < K; q++) a0[q] -= vv * lds<T>(a + q * (int)sizeof(T));
+        }
+        T acc[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] = a0[q] + a1[q];
+        for (int o = 16; o >= (32 >> rlg); o >>= 1)  // every lane of the row ends with the sum
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        if (!valid) return;
+        if (RESIDUAL) {
+            if (sub == 0)
+#pragma unroll
+                for (int q = 0; q < K; q++)
+                    stc(rself + q * (int)sizeof(T), (bb[q] - d * lds<T>(xrow + q * (int)sizeof(T))) + acc[q]);
+        } else {
+            T out[K];
+#pragma unroll
+            for (int q = 0; q < K; q++) out[q] = (bb[q] + acc[q]) * d;
+            const int cs = 1 << D.lg;
+            for (int j = sub; j < cs; j += 1 << rlg) {  // the row's lanes share the CS replica writes
+                const uint32_t a = dsm(xrow, (uint32_t)j);
+                const uint32_t bj = dsm(sbar, (uint32_t)j);
+#pragma unroll
+                for (int q = 0; q < K; q++) st_async(a + q * (int)sizeof(T), out[q], bj);
+            }
+        }
+    }
+};
+
+// Gauss-Seidel over the colour sequence of `steps` steps (colour of step k from
+// col_of(k)).  New values go to every replica by st.async, counted on the
+// receivers' step barriers; each CTA then arrives for the step on every CTA's
+// barrier (its own with the step's byte count: all rows of the colour), loads
+// its next step's entries and waits.  The loop ends with a cluster barrier, so
+// no store or arrival of the relaxation is in flight afterwards.
+template <typename T, int K, class ColourOf>
+__device__ __forceinline__ void tail_relax(const LevelCtx<T>& C, const Dist& D, int steps, ColourOf col_of,
+                                           int warp, int lane, StepBars& sb) {
+    TailRows<T, K> cur;
+    const int rlg = C.rlg;
+    auto load = [&](int c, int u) {
+        const int m = u >> rlg;
+        const int i = C.cfirst(c) + m;
+        cur.template load<false>(C, D, i < C.cfirst(c + 1) ? i : -1, u & ((1 << rlg) - 1), lane);
+    };
+    if (steps > 0) load(col_of(0), warp);
+    for (int k = 0; k < steps; k++) {
+        const int c = col_of(k);
+        const int units = (C.cfirst(c + 1) - C.cfirst(c)) << rlg;
+        const uint32_t bar = sb.bar();
+        cur.template run<false>(C, D, bar);
+        for (int u = warp + kTailWarps; u < units; u += kTailWarps) {
+            load(c, u);
+            cur.template run<false>(C, D, bar);
+        }
+        if (warp == 0 && lane < (1 << D.lg)) {
+            if ((uint32_t)lane == D.rank) {
+                mbar_arrive_expect_local(bar, (uint32_t)C.rows(c) * (uint32_t)(K * sizeof(T)));
+            } else {
+                mbar_arrive_remote(dsm(bar, (uint32_t)lane));
+            }
+        }
+        if (k + 1 < steps) load(col_of(k + 1), warp);
+        mbar_wait_cluster(bar, sb.parity(), C.L->err);
+        sb.step++;
+    }
+    cluster_sync();
+}
+
+// r = b - A x over all rows (this CTA's slices of every colour).
+template <typename T, int K>
+__device__ __forceinline__ void tail_residual(const LevelCtx<T>& C, const Dist& D, int warp, int lane) {
+    const int rlg = C.rlg;
+    const int units = C.n_my << rlg;
+    TailRows<T, K> cur;
+    for (int u = warp; u < units; u += kTailWarps) {
+        cur.template load<true>(C, D, u >> rlg, u & ((1 << rlg) - 1), lane);
+        cur.template run<true>(C, D);
     }
 }
 
-// b_{l+1} = P^T r_l (four lanes per coarse row) and the zero start x_{l+1} = 0.
-// Every thread makes the same number of passes (the shuffles need whole warps).
+// b_{l+1} = P^T r_l for the coarse rows this CTA owns (four lanes per row);
+// into distributed memory when level l+1 is in the tail (Ln != nullptr), with
+// this CTA's replica of x_{l+1} set to the zero start, else into level l+1's
+// global arrays (b and the zero x of the rows this CTA owns).
 template <typename T, int K>
-__device__ __forceinline__ void tail_restrict(const TailLevel<T>& L, int gthread, int nthreads) {
+__device__ __forceinline__ void tail_restrict(const TailLevel<T>& L, const TailLevel<T>* Ln, const Dist& D) {
     constexpr int RR = 4;
-    const int sub = gthread % RR;
-    const int per_pass = nthreads / RR;
-    const int passes = (L.n_next + per_pass - 1) / per_pass;
+    const int sub = threadIdx.x % RR;
+    constexpr int per_pass = kTailThreads / RR;
+    const int nloc_next = ((L.n_next + (32 << D.lg) - 1) >> (5 + D.lg)) << 5;
+    const int passes = (nloc_next + per_pass - 1) / per_pass;
+    const int sr = L.sbase + L.npad + L.nloc;
     for (int pass = 0; pass < passes; pass++) {
-        const int g = pass * per_pass + gthread / RR;
-        const bool ok = g < L.n_next;
-        const int I = ok ? g : L.n_next - 1;
+        const int li = pass * per_pass + (int)threadIdx.x / RR;
+        const int I0 = D.global(li);
+        const bool ok = li < nloc_next && I0 < L.n_next;
+        const int I = ok ? I0 : 0;
         T acc[K];
 #pragma unroll
         for (int q = 0; q < K; q++) acc[q] = T(0);
-        for (int k = L.pt_ptr[I] + sub; k < L.pt_ptr[I + 1]; k += RR) {
+        const int k1 = ok ? L.pt_ptr[I + 1] : 0;
+        for (int k = (ok ? L.pt_ptr[I] : 0) + sub; k < k1; k += RR) {
             const int i = L.pt_row[k];
             const T wk = L.pt_w[k];
+            const uint32_t a = D.template at<T, K>(sr, i);
 #pragma unroll
-            for (int q = 0; q < K; q++) acc[q] += wk * __ldcg(L.r + (int64_t)i * K + q);
+            for (int q = 0; q < K; q++) acc[q] += wk * ldc<T>(a + q * (int)sizeof(T));
         }
 #pragma unroll
         for (int o = RR / 2; o > 0; o >>= 1)
 #pragma unroll
             for (int q = 0; q < K; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-        if (ok && sub == 0)
+        if (ok && sub == 0) {
+            if (Ln) {
+                const uint32_t ba = D.template own<T, K>(Ln->sbase + Ln->npad, li);
 #pragma unroll
-            for (int q = 0; q < K; q++) {
-                L.b_next[(int64_t)I * K + q] = acc[q];
-                L.x_next[(int64_t)I * K + q] = T(0);
+                for (int q = 0; q < K; q++) stc(ba + q * (int)sizeof(T), acc[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < K; q++) {
+                    L.b_next[(int64_t)I * K + q] = acc[q];
+                    L.x_next[(int64_t)I * K + q] = T(0);
+                }
             }
+        }
     }
+    if (Ln)
+        for (int e = threadIdx.x; e < Ln->n * K; e += kTailThreads) sts(D.template rep<T, 1>(Ln->sbase * K, e), T(0));
 }
 
-// x_l += P x_{l+1}
+// x_l += P x_{l+1} for the rows of level l this CTA owns, written to level l's
+// global x (the replicas are refreshed from it after the next barrier);
+// x_{l+1} from the local replica (Ln != nullptr) or from global memory.
 template <typename T, int K>
-__device__ __forceinline__ void tail_prolong(const TailLevel<T>& L, int gthread, int nthreads) {
-    for (int p = gthread; p < L.n; p += nthreads) {
+__device__ __forceinline__ void tail_prolong(const TailLevel<T>& L, const TailLevel<T>* Ln, const Dist& D) {
+    for (int li = threadIdx.x; li < L.nloc; li += kTailThreads) {
+        const int p = D.global(li);
+        if (p >= L.n) continue;
         T acc[K];
 #pragma unroll
         for (int q = 0; q < K; q++) acc[q] = T(0);
@@ -133,61 +575,121 @@ __device__ __forceinline__ void tail_prolong(const TailLevel<T>& L, int gthread,
         for (int a = 0; a < 3; a++) {
             const int c = L.p_idx[(int64_t)a * L.n + p];
             const T wa = L.p_w[(int64_t)a * L.n + p];
+            if (Ln) {
+                const uint32_t ca = D.template rep<T, K>(Ln->sbase, c);
 #pragma unroll
-            for (int q = 0; q < K; q++) acc[q] += wa * __ldcg(L.x_next + (int64_t)c * K + q);
+                for (int q = 0; q < K; q++) acc[q] += wa * lds<T>(ca + q * (int)sizeof(T));
+            } else {
+#pragma unroll
+                for (int q = 0; q < K; q++) acc[q] += wa * L.x_next[(int64_t)c * K + q];
+            }
         }
+        const uint32_t xa = D.template rep<T, K>(L.sbase, p);
 #pragma unroll
-        for (int q = 0; q < K; q++) L.x[(int64_t)p * K + q] = __ldcg(L.x + (int64_t)p * K + q) + acc[q];
+        for (int q = 0; q < K; q++) L.x[(int64_t)p * K + q] = lds<T>(xa + q * (int)sizeof(T)) + acc[q];
     }
 }
 
-// Down-sweep of levels [l0, l1): pre-relaxation, residual, restriction.
+// Global x of a level into this CTA's replica (all rows).
 template <typename T, int K>
-__global__ void __launch_bounds__(kTailThreads) tail_down(const TailLevel<T>* __restrict__ lv, int l0, int l1,
-                                                          int mu_pre) {
-    const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (kTailThreads / 32);
-    const int gwarp = blockIdx.x * (kTailThreads / 32) + (threadIdx.x >> 5);
-    const int nthreads = gridDim.x * kTailThreads;
-    const int gthread = blockIdx.x * kTailThreads + threadIdx.x;
+__device__ __forceinline__ void tail_load_x(const TailLevel<T>& L, const Dist& D) {
+    for (int e = threadIdx.x; e < L.n * K; e += kTailThreads) sts(D.template rep<T, 1>(L.sbase * K, e), L.x[e]);
+}
+
+// This CTA's rows of b between global memory and the distributed array, and
+// (TO_SHARED = false) its rows of x from the replica to global memory.
+template <typename T, int K, bool TO_SHARED>
+__device__ __forceinline__ void tail_copy_own(const TailLevel<T>& L, const Dist& D, bool with_b) {
+    for (int e = threadIdx.x; e < L.nloc * K; e += kTailThreads) {
+        const int li = e / K, q = e - li * K;
+        const int i = D.global(li);
+        if (i >= L.n) continue;
+        const uint32_t ba = D.template own<T, K>(L.sbase + L.npad, li) + q * (int)sizeof(T);
+        if (TO_SHARED) {
+            stc(ba, L.b[(int64_t)i * K + q]);
+        } else {
+            L.x[(int64_t)i * K + q] = lds<T>(D.template rep<T, K>(L.sbase, i) + q * (int)sizeof(T));
+            if (with_b) L.b[(int64_t)i * K + q] = ldc<T>(ba);
+        }
+    }
+}
+
+__device__ __forceinline__ Dist make_dist(int lg, int dbase) {
+    Dist D;
+    D.base = (uint32_t)__cvta_generic_to_shared(tail_smem()) + (uint32_t)dbase;
+    D.lg = lg;
+    D.rank = cluster_rank();
+    return D;
+}
+
+// Down-sweep of levels [l0, l1): pre-relaxation, residual, restriction.  The
+// per-level arrays start at byte dbase of the dynamic shared memory, after the
+// slice tables and staged entries of the tail levels.
+template <typename T, int K>
+__global__ void __launch_bounds__(kTailThreads, 1) tail_down(const TailLevel<T>* __restrict__ lv, int l0, int l1,
+                                                             int mu_pre, int lg, int dbase) {
+    const Dist D = make_dist(lg, dbase);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ __align__(8) unsigned long long mbar[3];  // staging, even steps, odd steps
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+    uint32_t phase = 0;
+    StepBars sb{bar + 8u, 0u};
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 8u, 1 << lg);
+        mbar_init(bar + 16u, 1 << lg);
+    }
     pdl_wait();
     pdl_trigger();
+    tail_load_x<T, K>(lv[l0], D);
+    tail_copy_own<T, K, true>(lv[l0], D, true);
+    cluster_sync();
     for (int l = l0; l < l1; l++) {
-        const TailLevel<T> L = lv[l];
-        for (int it = 0; it < mu_pre; it++)
-            for (int c = 0; c < L.ncolours; c++) {
-                tail_gs<T, K>(L, c, gwarp, nwarps, lane);
-                cluster_sync();
-            }
-        tail_residual<T, K>(L, gwarp, nwarps, lane);
+        const LevelCtx<T> C = stage_level<T, K>(&lv[l], D, bar, phase);
+        const int nc = C.nc;
+        tail_relax<T, K>(C, D, mu_pre * nc, [nc](int k) { return k % nc; }, warp, lane, sb);
+        tail_residual<T, K>(C, D, warp, lane);
         cluster_sync();
-        tail_restrict<T, K>(L, gthread, nthreads);
+        tail_restrict<T, K>(lv[l], l + 1 < l1 ? &lv[l + 1] : nullptr, D);
         cluster_sync();
     }
+    for (int l = l0; l < l1; l++) tail_copy_own<T, K, false>(lv[l], D, true);
 }
 
 // Up-sweep of levels [l0, l1) from level l1 - 1 upwards: prolongation with the
 // correction add, then post-relaxation (colour classes reversed if asked).
 template <typename T, int K>
-__global__ void __launch_bounds__(kTailThreads) tail_up(const TailLevel<T>* __restrict__ lv, int l0, int l1,
-                                                        int mu_post, int reverse) {
-    const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (kTailThreads / 32);
-    const int gwarp = blockIdx.x * (kTailThreads / 32) + (threadIdx.x >> 5);
-    const int nthreads = gridDim.x * kTailThreads;
-    const int gthread = blockIdx.x * kTailThreads + threadIdx.x;
+__global__ void __launch_bounds__(kTailThreads, 1) tail_up(const TailLevel<T>* __restrict__ lv, int l0, int l1,
+                                                           int mu_post, int reverse, int lg, int dbase) {
+    const Dist D = make_dist(lg, dbase);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ __align__(8) unsigned long long mbar[3];  // staging, even steps, odd steps
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+    uint32_t phase = 0;
+    StepBars sb{bar + 8u, 0u};
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 8u, 1 << lg);
+        mbar_init(bar + 16u, 1 << lg);
+    }
     pdl_wait();
     pdl_trigger();
-    for (int l = l1 - 1; l >= l0; l--) {
-        const TailLevel<T> L = lv[l];
-        tail_prolong<T, K>(L, gthread, nthreads);
-        cluster_sync();
-        for (int it = 0; it < mu_post; it++)
-            for (int cc = 0; cc < L.ncolours; cc++) {
-                tail_gs<T, K>(L, reverse ? L.ncolours - 1 - cc : cc, gwarp, nwarps, lane);
-                cluster_sync();
-            }
+    for (int l = l0; l < l1; l++) {
+        tail_load_x<T, K>(lv[l], D);
+        tail_copy_own<T, K, true>(lv[l], D, true);
     }
+    __syncthreads();
+    for (int l = l1 - 1; l >= l0; l--) {
+        tail_prolong<T, K>(lv[l], l + 1 < l1 ? &lv[l + 1] : nullptr, D);
+        cluster_sync();  // level l's corrected x is in global memory
+        tail_load_x<T, K>(lv[l], D);
+        const LevelCtx<T> C = stage_level<T, K>(&lv[l], D, bar, phase);
+        cluster_sync();  // every replica refreshed before any step writes into it
+        const int nc = C.nc;
+        tail_relax<T, K>(C, D, mu_post * nc, [nc, reverse](int k) { return reverse ? nc - 1 - k % nc : k % nc; },
+                         warp, lane, sb);
+    }
+    tail_copy_own<T, K, false>(lv[l0], D, false);
 }
 
 }  // namespace kern
