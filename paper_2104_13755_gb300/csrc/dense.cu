@@ -23,101 +23,109 @@ __global__ void k_pad_copy(const double* __restrict__ A, int64_t n, double* __re
     X[e] = (i == j) ? 1.0 : 0.0;
 }
 
-// 1 / sqrt(d) for d > 0: binary32 estimate of the scaled argument refined by two
-// Newton steps y <- y (3 - m y^2) / 2 in binary64 (quadratic convergence from
-// 24 correct bits), with the exponent split off exactly (frexp / ldexp) so the
-// binary32 estimate never under- or overflows.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-    int e;
-    double m = frexp(d, &e);  // d = m 2^e, m in [0.5, 1)
-    if (e & 1) {
-        m *= 2.0;
-        e -= 1;
-    }
-    double y = (double)rsqrtf((float)m);
-    y = y * (1.5 - 0.5 * m * y * y);
-    y = y * (1.5 - 0.5 * m * y * y);
-    return ldexp(y, -e / 2);
-}
-
-// Factor diagonal tile j in shared memory and store its triangular inverse.
-// The pivots form a dependent binary64 chain, so per pivot: warp 0 computes the
-// reciprocal square root and scales the column; one barrier; all threads apply
-// the rank-1 update; one barrier.  The inverse (forward elimination of L X = I)
-// writes final rows to a separate tile, one barrier per step.
-__global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ C, int64_t np, int j,
-                                                   double* __restrict__ dblk, int32_t* __restrict__ bad) {
-    __shared__ double a[NB][NB + 1];    // trailing part
-    __shared__ double l[NB][NB + 1];    // finished factor
-    __shared__ double x[NB][NB + 1];    // inverse in progress
-    __shared__ double xf[NB][NB + 1];   // finished inverse rows
-    __shared__ double rinv[NB];
-    const int c = threadIdx.x % NB, r0 = threadIdx.x / NB;  // rows r0, r0 + 8, r0 + 16, r0 + 24
+// Factor diagonal tile j.  Binary64 FMA issue is about one lane per two clocks
+// per SM sub-partition, so the work is spread over the four sub-partitions:
+// warp w holds columns c = w, w + 4, ... of the tile in registers (lane = row).
+// Per pivot k the warp owning column k takes the pivot by shuffle, CUDA's
+// binary64 rsqrt gives 1 / sqrt(pivot), its lanes scale column k and publish it
+// in shared memory (two buffers, so one barrier per pivot), and every warp
+// applies the rank-1 update to its columns right of k (lower triangle).
+constexpr int kDiagWarps = 4;
+constexpr int kDiagCols = NB / kDiagWarps;
+__global__ void __launch_bounds__(32 * kDiagWarps) k_chol_diag(double* __restrict__ C, int64_t np, int j,
+                                                                double* __restrict__ rinv_out,
+                                                                int32_t* __restrict__ bad) {
+    __shared__ double a[NB][NB + 1];
+    __shared__ double lk[2][NB];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double* T = C + (int64_t)j * NB * np + (int64_t)j * NB;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const int r = r0 + 8 * q;
-        a[r][c] = T[(int64_t)r * np + c];
-        l[r][c] = 0.0;
-        x[r][c] = (r == c) ? 1.0 : 0.0;
-        xf[r][c] = 0.0;
-    }
+    for (int e = threadIdx.x; e < NB * NB; e += 32 * kDiagWarps) a[e / NB][e % NB] = T[(int64_t)(e / NB) * np + e % NB];
     __syncthreads();
+    double col[kDiagCols];  // col[m] = a[lane][m * kDiagWarps + w]
+#pragma unroll
+    for (int m = 0; m < kDiagCols; m++) col[m] = a[lane][m * kDiagWarps + w];
+    bool flagged = false;
+#pragma unroll
     for (int k = 0; k < NB; k++) {
-        if (threadIdx.x < 32) {
-            double d = a[k][k];
+        const int mk = k / kDiagWarps;
+        if (w == k % kDiagWarps) {
+            double d = __shfl_sync(0xffffffffu, col[mk], k);
             if (!(d > 0.0) || !isfinite(d)) {  // not SPD: flag it, keep the arithmetic finite
-                if (threadIdx.x == 0) atomicExch(bad, 1);
+                flagged = true;
                 d = 1.0;
             }
-            const double y = rsqrt_newton(d);
-            const int rr = threadIdx.x;
-            if (rr == k) {
-                l[k][k] = d * y;
-                rinv[k] = y;
-            } else if (rr > k) {
-                l[rr][k] = a[rr][k] * y;
-            }
+            const double y = rsqrt(d);
+            const double l = (lane == k) ? d * y : col[mk] * y;
+            if (lane >= k) col[mk] = l;
+            lk[k & 1][lane] = l;
+            if (lane == k) rinv_out[(int64_t)j * NB + k] = y;
         }
         __syncthreads();
+        const double lr = lk[k & 1][lane];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int r = r0 + 8 * q;
-            if (c > k && r >= c) a[r][c] -= l[r][k] * l[c][k];
+        for (int m = 0; m < kDiagCols; m++) {
+            const int c = m * kDiagWarps + w;
+            if (c > k && lane >= c) col[m] -= lr * lk[k & 1][c];
         }
-        __syncthreads();
     }
-    for (int k = 0; k < NB; k++) {
+    if (flagged) atomicExch(bad, 1);
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int r = r0 + 8 * q;
-            if (r == k && c <= k) xf[k][c] = x[k][c] * rinv[k];
-            if (r > k && c <= k) x[r][c] -= l[r][k] * (x[k][c] * rinv[k]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const int r = r0 + 8 * q;
-        T[(int64_t)r * np + c] = l[r][c];
-        dblk[(int64_t)j * NB * NB + r * NB + c] = xf[r][c];
+    for (int m = 0; m < kDiagCols; m++) {
+        const int c = m * kDiagWarps + w;
+        T[(int64_t)lane * np + c] = (c <= lane) ? col[m] : 0.0;
     }
 }
 
+// Inverse of diagonal tile j (X = L_jj^{-1}, forward elimination of L X = I):
+// columns are independent, so kQ blocks of four warps take two columns per
+// warp; lane = row, the row-k value of a column arrives by shuffle.
+__global__ void __launch_bounds__(128) k_tile_inv(const double* __restrict__ C, int64_t np, int j,
+                                                  const double* __restrict__ rinv, double* __restrict__ dblk) {
+    __shared__ double l[NB][NB + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double* T = C + (int64_t)j * NB * np + (int64_t)j * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += 128) l[e / NB][e % NB] = T[(int64_t)(e / NB) * np + e % NB];
+    __syncthreads();
+    const int c0 = blockIdx.x * 8 + w * 2;  // this warp's two columns
+    double x0 = (lane == c0) ? 1.0 : 0.0, x1 = (lane == c0 + 1) ? 1.0 : 0.0;
+    const double ri = rinv[(int64_t)j * NB + lane];
+    for (int k = c0; k < NB; k++) {
+        // row k of both columns is final after scaling; broadcast it
+        const double k0 = __shfl_sync(0xffffffffu, x0 * ri, k);
+        const double k1 = __shfl_sync(0xffffffffu, x1 * ri, k);
+        if (lane == k) {
+            x0 = k0;
+            x1 = k1;
+        } else if (lane > k) {
+            const double lrk = l[lane][k];
+            x0 -= lrk * k0;
+            x1 -= lrk * k1;
+        }
+    }
+    dblk[(int64_t)j * NB * NB + lane * NB + c0] = (lane >= c0) ? x0 : 0.0;
+    dblk[(int64_t)j * NB * NB + lane * NB + c0 + 1] = (lane >= c0 + 1) ? x1 : 0.0;
+}
+
+// Work units of the tile kernels: a 32 x 32 output tile split into kQ blocks of
+// 32 / kQ rows (binary64 throughput is per SM, so more SMs per tile).
+constexpr int kQ = 4;
+constexpr int kQR = NB / kQ;
+
 // L_ij = A_ij L_jj^{-T} for the tiles below the diagonal tile j.
-__global__ void __launch_bounds__(NB * NB) k_chol_panel(double* __restrict__ C, int64_t np, int j,
-                                                        const double* __restrict__ dblk) {
-    __shared__ double a[NB][NB + 1];
+__global__ void __launch_bounds__(kQR * NB) k_chol_panel(double* __restrict__ C, int64_t np, int j,
+                                                         const double* __restrict__ dblk) {
+    __shared__ double a[kQR][NB + 1];
     __shared__ double d[NB][NB + 1];
-    const int i = j + 1 + blockIdx.x;
-    const int r = threadIdx.x / NB, c = threadIdx.x % NB;
-    double* T = C + (int64_t)i * NB * np + (int64_t)j * NB;
-    a[r][c] = T[(int64_t)r * np + c];
-    d[r][c] = dblk[(int64_t)j * NB * NB + r * NB + c];
+    const int i = j + 1 + blockIdx.x / kQ, q0 = (blockIdx.x % kQ) * kQR;
+    const int rl = threadIdx.x / NB, c = threadIdx.x % NB;
+    double* T = C + ((int64_t)i * NB + q0) * np + (int64_t)j * NB;
+    a[rl][c] = T[(int64_t)rl * np + c];
+#pragma unroll
+    for (int q = 0; q < kQ; q++) d[rl + kQR * q][c] = dblk[(int64_t)j * NB * NB + (rl + kQR * q) * NB + c];
     __syncthreads();
     double s[4] = {0.0, 0.0, 0.0, 0.0};  // four independent partial sums
-    for (int k = 0; k <= c; k++) s[k & 3] += a[r][k] * d[c][k];
-    T[(int64_t)r * np + c] = (s[0] + s[1]) + (s[2] + s[3]);
+    for (int k = 0; k <= c; k++) s[k & 3] += a[rl][k] * d[c][k];
+    T[(int64_t)rl * np + c] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 __device__ __forceinline__ void tri_index(int b, int& ii, int& kk) {
@@ -129,23 +137,26 @@ __device__ __forceinline__ void tri_index(int b, int& ii, int& kk) {
 }
 
 // Trailing update A_ik -= L_ij L_kj^T for j < k <= i.
-__global__ void __launch_bounds__(NB * NB) k_chol_update(double* __restrict__ C, int64_t np, int j) {
-    __shared__ double li[NB][NB + 1];
+__global__ void __launch_bounds__(kQR * NB) k_chol_update(double* __restrict__ C, int64_t np, int j) {
+    __shared__ double li[kQR][NB + 1];
     __shared__ double lk[NB][NB + 1];
     int ii, kk;
-    tri_index(blockIdx.x, ii, kk);
+    tri_index(blockIdx.x / kQ, ii, kk);
+    const int q0 = (blockIdx.x % kQ) * kQR;
     const int i = j + 1 + ii, k = j + 1 + kk;
-    const int r = threadIdx.x / NB, c = threadIdx.x % NB;
-    li[r][c] = C[((int64_t)i * NB + r) * np + (int64_t)j * NB + c];
-    lk[r][c] = C[((int64_t)k * NB + r) * np + (int64_t)j * NB + c];
+    const int rl = threadIdx.x / NB, c = threadIdx.x % NB;
+    li[rl][c] = C[((int64_t)i * NB + q0 + rl) * np + (int64_t)j * NB + c];
+#pragma unroll
+    for (int q = 0; q < kQ; q++) lk[rl + kQR * q][c] = C[((int64_t)k * NB + rl + kQR * q) * np + (int64_t)j * NB + c];
     __syncthreads();
     double s[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int q = 0; q < NB; q++) s[q & 3] += li[r][q] * lk[c][q];
-    C[((int64_t)i * NB + r) * np + (int64_t)k * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
+    for (int q = 0; q < NB; q++) s[q & 3] += li[rl][q] * lk[c][q];
+    C[((int64_t)i * NB + q0 + rl) * np + (int64_t)k * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
 }
 
-// Block row i of X = L^{-1}: X_i,jb = L_ii^{-1} B_i,jb for jb <= i (B accumulates I - sum L X).
+// Block row i of X = L^{-1}: X_i,jb = L_ii^{-1} B_i,jb for jb <= i (B accumulates
+// I - sum L X).  In place, so one block per tile (rows depend on earlier rows).
 __global__ void __launch_bounds__(NB * NB) k_trinv_row(double* __restrict__ X, int64_t np, int i,
                                                        const double* __restrict__ dblk) {
     __shared__ double bs[NB][NB + 1];
@@ -161,21 +172,24 @@ __global__ void __launch_bounds__(NB * NB) k_trinv_row(double* __restrict__ X, i
     T[(int64_t)r * np + c] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
-// B_k,jb -= L_k,i X_i,jb for k > i, jb <= i.
-__global__ void __launch_bounds__(NB * NB) k_trinv_update(double* __restrict__ X, const double* __restrict__ C,
-                                                          int64_t np, int i) {
-    __shared__ double l[NB][NB + 1];
+// B_k,jb -= L_k,i X_i,jb for k > i, jb <= i (output rows split over kQ blocks;
+// the tiles read are not written by this kernel).
+__global__ void __launch_bounds__(kQR * NB) k_trinv_update(double* __restrict__ X, const double* __restrict__ C,
+                                                           int64_t np, int i) {
+    __shared__ double l[kQR][NB + 1];
     __shared__ double xs[NB][NB + 1];
-    const int k = i + 1 + blockIdx.x / (i + 1);
-    const int jb = blockIdx.x % (i + 1);
-    const int r = threadIdx.x / NB, c = threadIdx.x % NB;
-    l[r][c] = C[((int64_t)k * NB + r) * np + (int64_t)i * NB + c];
-    xs[r][c] = X[((int64_t)i * NB + r) * np + (int64_t)jb * NB + c];
+    const int t = blockIdx.x / kQ, q0 = (blockIdx.x % kQ) * kQR;
+    const int k = i + 1 + t / (i + 1);
+    const int jb = t % (i + 1);
+    const int rl = threadIdx.x / NB, c = threadIdx.x % NB;
+    l[rl][c] = C[((int64_t)k * NB + q0 + rl) * np + (int64_t)i * NB + c];
+#pragma unroll
+    for (int q = 0; q < kQ; q++) xs[rl + kQR * q][c] = X[((int64_t)i * NB + rl + kQR * q) * np + (int64_t)jb * NB + c];
     __syncthreads();
     double s[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int q = 0; q < NB; q++) s[q & 3] += l[r][q] * xs[q][c];
-    X[((int64_t)k * NB + r) * np + (int64_t)jb * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
+    for (int q = 0; q < NB; q++) s[q & 3] += l[rl][q] * xs[q][c];
+    X[((int64_t)k * NB + q0 + rl) * np + (int64_t)jb * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 __global__ void k_transpose(const double* __restrict__ X, double* __restrict__ XT, int64_t np) {
@@ -268,14 +282,15 @@ void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s) {
     cudaStream_t s2 = h->aux;
     k_pad_copy<<<(unsigned)((np * np + 255) / 256), 256, 0, s>>>(C.vals, C.n, C.chol, C.linv, np);
     for (int j = 0; j < nb; j++) {
-        k_chol_diag<<<1, 256, 0, s>>>(C.chol, np, j, C.dblk, &h->state->chol_bad);
+        k_chol_diag<<<1, 32 * kDiagWarps, 0, s>>>(C.chol, np, j, C.rinv, &h->state->chol_bad);
+        k_tile_inv<<<kQ, 128, 0, s>>>(C.chol, np, j, C.rinv, C.dblk);
         const int T = nb - j - 1;
-        if (T > 0) k_chol_panel<<<T, NB * NB, 0, s>>>(C.chol, np, j, C.dblk);
+        if (T > 0) k_chol_panel<<<T * kQ, kQR * NB, 0, s>>>(C.chol, np, j, C.dblk);
         cudaEventRecord(h->ev_step[j], s);
-        if (T > 0) k_chol_update<<<T * (T + 1) / 2, NB * NB, 0, s>>>(C.chol, np, j);
+        if (T > 0) k_chol_update<<<T * (T + 1) / 2 * kQ, kQR * NB, 0, s>>>(C.chol, np, j);
         cudaStreamWaitEvent(s2, h->ev_step[j], 0);
         k_trinv_row<<<j + 1, NB * NB, 0, s2>>>(C.linv, np, j, C.dblk);
-        if (j + 1 < nb) k_trinv_update<<<(nb - j - 1) * (j + 1), NB * NB, 0, s2>>>(C.linv, C.chol, np, j);
+        if (j + 1 < nb) k_trinv_update<<<(nb - j - 1) * (j + 1) * kQ, kQR * NB, 0, s2>>>(C.linv, C.chol, np, j);
     }
     cudaEventRecord(h->ev_join, s2);
     cudaStreamWaitEvent(s, h->ev_join, 0);

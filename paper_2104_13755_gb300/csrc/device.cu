@@ -767,6 +767,7 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
             L.linv = dalloc<double>(h, L.np * L.np);
             L.linvT = dalloc<double>(h, L.np * L.np);
             L.dblk = dalloc<double>(h, L.np * kDenseNB);
+            L.rinv = dalloc<double>(h, L.np);
             h->ev_step.assign(L.np / kDenseNB, nullptr);
             for (auto& e : h->ev_step) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
             ck(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event");

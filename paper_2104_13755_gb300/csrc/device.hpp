@@ -65,6 +65,7 @@ struct DLevel {
     // coarsest: padded dense factor, its inverse and the inverse transposed
     int64_t np = 0;
     double *chol = nullptr, *linv = nullptr, *linvT = nullptr, *dblk = nullptr, *y = nullptr;
+    double* rinv = nullptr;  // reciprocal diagonal of the coarsest factor
     // read-back map
     std::vector<int64_t> flat_to_csr;
     int64_t nnz_csr = 0;
