@@ -43,6 +43,26 @@ METRIC = "V-cycles/s at 1M verts (solve to rel. residual 1e-9, update included)"
 L2_FLUSH_BYTES = 256 << 20
 
 
+# DRAM traffic of the roofline kernel from one ncu capture (profiles/
+# gs_colour_level0_torus1m.md): dram__bytes_read.sum + dram__bytes_write.sum of
+# the level-0 binary64 colour launches, per sweep (4 classes x 28.13 MB).  Valid
+# only for the kernel source it was taken on; reported as null otherwise.
+TRAFFIC_CAPTURE = dict(bytes_per_sweep=4 * 28.13e6, bytes_per_launch=28.13e6,
+                       source="paper_2104_13755_gb300/csrc/kernels.cuh",
+                       sha256="9893356ba1e2c934a3917fb802056315fed08fe21b9559c929871d15b67e4f6a")
+
+
+def captured_traffic():
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_CAPTURE["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != TRAFFIC_CAPTURE["sha256"]:
+                return None
+    except OSError:
+        return None
+    return TRAFFIC_CAPTURE["bytes_per_sweep"]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -363,7 +383,9 @@ def run_ours(args, w, rank, world, local_rank):
                   "refinement_steps_per_solve": cyc_mx[0]},
         "roofline": {"kernel": "gs_colour<double,1> level-0 sweep (all colour launches)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "traffic": captured_traffic(), "traffic_source": "ncu dram__bytes_read.sum + "
+                     "dram__bytes_write.sum per sweep (profiles/gs_colour_level0_torus1m.md)",
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_sweep": sb},
         "roofline_vcycle": {"fp64": {"bytes": cb64, "achieved": cb64 / (cyc64_ms * 1e-3) / 1e9,
                                      "frac": cb64 / (cyc64_ms * 1e-3) / 1e9 / peak},
