@@ -8,10 +8,10 @@ oracle and the CUDA path can both consume its output without sharing method code
 from .meshes import (icosahedron, icosphere, perturbed_icosphere, geodesic_sphere,
                      perturbed_geodesic_sphere,
                      torus, disk, sh_noise, mean_edge_length, boundary_mask,
-                     euler_characteristic)
+                     euler_characteristic, sinusoidal_displacement)
 from .rhs import uniform_rhs, unit_directions
 
 __all__ = ["icosahedron", "icosphere", "perturbed_icosphere", "geodesic_sphere",
            "perturbed_geodesic_sphere",
            "torus", "disk", "sh_noise", "mean_edge_length", "boundary_mask",
-           "euler_characteristic", "uniform_rhs", "unit_directions"]
+           "euler_characteristic", "sinusoidal_displacement", "uniform_rhs", "unit_directions"]

@@ -253,6 +253,24 @@ def disk(N=400, jitter=0.01, seed=0):
 # ---------------------------------------------------------------------------
 # plain mesh facts (no solver arithmetic)
 # ---------------------------------------------------------------------------
+def sinusoidal_displacement(V, frame, seed=0, amp=0.05, nframes=100, nwaves=3):
+    """Seeded smooth deformation field for per-frame re-solves:
+    d_f(p) = amp * sum_k a_k sin(w_k . p + phi_k + 2 pi f / nframes) e_k with
+    a_k >= 0 summing to 1, |w_k| <= 4 pi, phases phi_k in [0, 2 pi) and unit
+    directions e_k.  Returns the moved positions V + d_f(V)."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.2, 1.0, nwaves)
+    a /= a.sum()
+    w = rng.normal(size=(nwaves, 3))
+    w *= (rng.uniform(0.25, 1.0, nwaves) * 4 * np.pi / np.linalg.norm(w, axis=1))[:, None]
+    phi = rng.uniform(0, 2 * np.pi, nwaves)
+    e = rng.normal(size=(nwaves, 3))
+    e /= np.linalg.norm(e, axis=1)[:, None]
+    V = np.asarray(V, dtype=np.float64)
+    s = np.sin(V @ w.T + phi + 2 * np.pi * frame / nframes)  # n x nwaves
+    return V + amp * (s * a) @ e
+
+
 def mean_edge_length(V, F):
     e = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
     e = np.unique(np.sort(e, axis=1), axis=0)
