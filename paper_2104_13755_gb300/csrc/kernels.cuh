@@ -42,10 +42,16 @@ __device__ __forceinline__ T ldx(const T* p) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Entries per lane loaded ahead of the dependency wait.
-template <typename T, int K>
+// Entries per lane loaded ahead of the dependency wait.  With one lane per row
+// (the finest level, valence ~6) six entries cover a typical row and keep the
+// kernel at 48 registers, five resident blocks per SM.
+template <typename T, int K, int R>
 struct Pre {
-    static constexpr int value = (K <= 2 || sizeof(T) == 4) ? 8 : 4;
+    static constexpr int value = R == 1 ? 6 : ((K <= 2 || sizeof(T) == 4) ? 8 : 4);
+};
+template <int K, int R>
+struct MinBlocks {
+    static constexpr int value = (R == 1 && K == 1) ? 5 : 1;
 };
 
 // A warp covers 32 / R rows of a SELL-32 slice (sub-slice g of R), R lanes per
@@ -83,19 +89,25 @@ struct RowSlice {
             if (sub + R * u < W)
 #pragma unroll
                 for (int q = 0; q < K; q++) xv[u][q] = ldx<COHERENT>(x + (int64_t)c[u] * K + q);
+        T a1[K];  // two independent FMA chains (binary64 FMAs are long-latency here)
 #pragma unroll
-        for (int q = 0; q < K; q++) acc[q] = T(0);
+        for (int q = 0; q < K; q++) acc[q] = a1[q] = T(0);
 #pragma unroll
         for (int u = 0; u < PRE; u++)
             if (sub + R * u < W)
 #pragma unroll
-                for (int q = 0; q < K; q++) acc[q] -= v[u] * xv[u][q];
+                for (int q = 0; q < K; q++) {
+                    if (u & 1) a1[q] -= v[u] * xv[u][q];
+                    else acc[q] -= v[u] * xv[u][q];
+                }
         for (int k = sub + R * PRE; k < W; k += R) {  // rows longer than PRE * R: the rare tail
             const int cc = ldg(col + m.off + k * 32 + r);
             const T vv = ldg(sval + m.off + k * 32 + r);
 #pragma unroll
             for (int q = 0; q < K; q++) acc[q] -= vv * ldx<COHERENT>(x + (int64_t)cc * K + q);
         }
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] += a1[q];
 #pragma unroll
         for (int o = 16; o >= RL; o >>= 1)
 #pragma unroll
@@ -110,7 +122,7 @@ struct RowSlice {
 // update in parallel and the x values gathered here are not written by this
 // launch (padding entries point at the row itself with value 0).
 template <typename T, int K, int R>
-__global__ void __launch_bounds__(kThreads) gs_colour(const SliceMeta* __restrict__ slices, int s0, int s1,
+__global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) gs_colour(const SliceMeta* __restrict__ slices, int s0, int s1,
                                                       const int32_t* __restrict__ col, const T* __restrict__ sval,
                                                       const T* __restrict__ dinv, const T* __restrict__ b,
                                                       T* __restrict__ x) {
@@ -119,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) gs_colour(const SliceMeta* __restric
     const int lane = threadIdx.x & 31;
     if (s >= s1) return;
     const SliceMeta m = slices[s];
-    RowSlice<T, K, R, Pre<T, K>::value> rs;
+    RowSlice<T, K, R, Pre<T, K, R>::value> rs;
     rs.load(m, w % R, lane, col, sval);
     const bool valid = rs.r < m.nrows;
     const int row = m.row0 + (valid ? rs.r : 0);
@@ -135,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) gs_colour(const SliceMeta* __restric
 
 // r = b - A x over all rows of a level.
 template <typename T, int K, int R>
-__global__ void __launch_bounds__(kThreads) residual(const SliceMeta* __restrict__ slices, int nslices,
+__global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) residual(const SliceMeta* __restrict__ slices, int nslices,
                                                      const int32_t* __restrict__ col, const T* __restrict__ sval,
                                                      const T* __restrict__ diag, const T* __restrict__ b,
                                                      const T* __restrict__ x, T* __restrict__ r) {
@@ -144,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) residual(const SliceMeta* __restrict
     const int lane = threadIdx.x & 31;
     if (s >= nslices) return;
     const SliceMeta m = slices[s];
-    RowSlice<T, K, R, Pre<T, K>::value> rs;
+    RowSlice<T, K, R, Pre<T, K, R>::value> rs;
     rs.load(m, w % R, lane, col, sval);
     const bool valid = rs.r < m.nrows;
     const int row = m.row0 + (valid ? rs.r : 0);
@@ -254,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) resnorm(const SliceMeta* __restrict_
     for (int q = 0; q < K; q++) rr[q] = bb[q] = 0.0;
     for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nslices * R; w += gridDim.x * kWarps) {
         const SliceMeta m = slices[w / R];
-        RowSlice<double, K, R, Pre<double, K>::value> rs;
+        RowSlice<double, K, R, Pre<double, K, R>::value> rs;
         rs.load(m, w % R, lane, col, sval);
         double acc[K];
         rs.dot(m, col, sval, x, acc);
