@@ -124,22 +124,24 @@ void rec_residual(DLevel& L, const LevelView<T>& v, cudaStream_t s) {
 // tables and staged entries.
 int tail_nloc(int64_t n, int cs) { return (int)((n + 32 * cs - 1) / (32 * cs)) * 32; }
 int tail_npad(int64_t n) { return (int)((n + 31) / 32) * 32; }
-int tail_nwork(const DLevel& L) {
+int tail_nwork(const DLevel& L, bool single) {
+    const DLevel::TailTable& T = L.tt[single ? 1 : 0];
     int m = 0;
-    for (const auto& en : L.t_E_nmy) m = std::max(m, en.second);
-    return 32 * m;
+    for (const auto& en : T.E_nmy) m = std::max(m, en.second);
+    return m << (5 - T.rlg);  // 32 / R rows per unit
 }
-int64_t tail_slots(const smg_hierarchy* h, int t) {
+int64_t tail_slots(const smg_hierarchy* h, int t, bool single) {
     int64_t slots = 0;
     for (int l = t; l < h->H; l++)
-        slots += tail_npad(h->L[l].n) + 2 * (int64_t)tail_nloc(h->L[l].n, h->tail_cluster) + tail_nwork(h->L[l]);
+        slots += tail_npad(h->L[l].n) + 2 * (int64_t)tail_nloc(h->L[l].n, h->tail_cluster) +
+                 tail_nwork(h->L[l], single);
     return slots;
 }
 constexpr size_t kTailSmemMax = 226 * 1024;  // 227 KB per block, less room for the static mbarrier
 
 size_t tail_bytes(const smg_hierarchy* h, int t, bool single, int K) {
     const std::vector<int>& db = single ? h->tail_dbase32 : h->tail_dbase64;
-    return (size_t)db[t] + (size_t)tail_slots(h, t) * K * (single ? sizeof(float) : sizeof(double));
+    return (size_t)db[t] + (size_t)tail_slots(h, t, single) * K * (single ? sizeof(float) : sizeof(double));
 }
 
 // First tail level for K right-hand sides: the tuned level, moved down while its
@@ -155,7 +157,7 @@ template <typename T, int K>
 void rec_tail(smg_hierarchy* h, bool down, int t, cudaStream_t s) {
     const bool single = sizeof(T) == 4;
     const TailLevel<T>* lv = (const TailLevel<T>*)(single ? h->tail_lv32 : h->tail_lv64) + (size_t)t * h->H;
-    const dim3 block(kern::kTailThreads);
+    const dim3 block(kern::TailThreads<T>::value);
     const size_t smem = tail_bytes(h, t, single, K);
     const int lg = h->tail_cluster == 16 ? 4 : 3;
     const int dbase = (single ? h->tail_dbase32 : h->tail_dbase64)[t];
@@ -449,49 +451,62 @@ void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
     }
 }
 
-// Per-CTA slice tables of every level for a cluster of cs CTAs (layout in
-// TailLevel): CTA r takes the slices of each colour class whose first row lies
-// in one of its 32-row blocks.
-void build_tail_tables(smg_hierarchy* h, const Plan& P, int cs) {
-    for (int l = 0; l < h->H; l++) {
-        const LevelPlan& lp = P.L[l];
-        DLevel& L = h->L[l];
-        const int nc = (int)lp.colour_slice.size() - 1;
-        std::vector<int32_t> tab, off(cs + 1, 0);
-        L.t_E_nmy.assign(cs, {0, 0});
-        L.ttab_ints = 0;
-        for (int r = 0; r < cs; r++) {
-            off[r] = (int32_t)tab.size();
-            const size_t head = tab.size();
-            tab.push_back(0);
-            tab.push_back(0);
-            std::vector<int32_t> cfirst(nc + 1, 0), ent;
-            int n_my = 0, E = 0;
-            for (int c = 0; c < nc; c++) {
-                cfirst[c] = n_my;
-                const int s0 = lp.colour_slice[c], s1 = lp.colour_slice[c + 1];
-                const int owner0 = (lp.colour_row[c] >> 5) & (cs - 1);
-                const int first = (r - owner0) & (cs - 1);
-                for (int s = s0 + first; s < s1; s += cs) {
-                    const SliceMeta& m = lp.slices[s];
-                    ent.insert(ent.end(), {(int32_t)m.off, m.width, m.row0, m.nrows, E});
-                    E += m.width * 32;
-                    n_my++;
-                }
+// Per-CTA work-unit tables of every level for a cluster of cs CTAs (layout in
+// TailLevel): the units of each colour class (a slice's rows in groups of
+// 32 / R) are dealt round-robin over the CTAs.  Binary64 takes the smallest R
+// for which kern::kTailPre entries per lane cover the widest row (its steps are
+// bound by FP64 issue, and every lane of a row repeats the reduction and the
+// update); binary32 takes at least 8 (latency-bound, cheap FLOPs).
+int tail_rlg(int maxw, bool single) {
+    int rlg = 0;
+    while (rlg < 5 && (kern::kTailPre << rlg) < maxw) rlg++;
+    if (single) rlg = std::max(rlg, 3);
+    return rlg;
+}
+void build_tail_table(smg_hierarchy* h, const LevelPlan& lp, DLevel& L, int cs, int prec) {
+    const int nc = (int)lp.colour_slice.size() - 1;
+    const int rlg = tail_rlg(L.maxw, prec == 1), RL = 32 >> rlg;
+    DLevel::TailTable& T = L.tt[prec];
+    T.rlg = rlg;
+    std::vector<std::vector<int32_t>> ent(cs);  // per CTA: 6 ints per unit
+    std::vector<std::vector<int32_t>> cfirst(cs, std::vector<int32_t>(nc + 1, 0));
+    std::vector<int> E(cs, 0), n_my(cs, 0);
+    for (int c = 0; c < nc; c++) {
+        for (int r = 0; r < cs; r++) cfirst[r][c] = n_my[r];
+        int q = 0;  // unit counter of this colour
+        for (int s = lp.colour_slice[c]; s < lp.colour_slice[c + 1]; s++) {
+            const SliceMeta& m = lp.slices[s];
+            for (int g = 0; g * RL < m.nrows; g++, q++) {
+                const int r = q % cs;
+                ent[r].insert(ent[r].end(), {(int32_t)m.off, m.width, m.row0 + g * RL, std::min(RL, m.nrows - g * RL),
+                                             E[r], g});
+                E[r] += m.width * RL;
+                n_my[r]++;
             }
-            cfirst[nc] = n_my;
-            tab[head] = n_my;
-            tab[head + 1] = E;
-            tab.insert(tab.end(), cfirst.begin(), cfirst.end());
-            for (int c = 0; c < nc; c++) tab.push_back(lp.colour_row[c + 1] - lp.colour_row[c]);
-            tab.insert(tab.end(), ent.begin(), ent.end());
-            L.t_E_nmy[r] = {E, n_my};
-            L.ttab_ints = std::max(L.ttab_ints, (int)(tab.size() - head));
         }
-        off[cs] = (int32_t)tab.size();
-        L.ttab = upload(h, tab);
-        L.ttab_off = upload(h, off);
     }
+    std::vector<int32_t> tab, off(cs + 1, 0);
+    T.E_nmy.assign(cs, {0, 0});
+    T.ints = 0;
+    for (int r = 0; r < cs; r++) {
+        off[r] = (int32_t)tab.size();
+        const size_t head = tab.size();
+        cfirst[r][nc] = n_my[r];
+        tab.push_back(n_my[r]);
+        tab.push_back(E[r]);
+        tab.insert(tab.end(), cfirst[r].begin(), cfirst[r].end());
+        for (int c = 0; c < nc; c++) tab.push_back(lp.colour_row[c + 1] - lp.colour_row[c]);
+        tab.insert(tab.end(), ent[r].begin(), ent[r].end());
+        T.E_nmy[r] = {E[r], n_my[r]};
+        T.ints = std::max(T.ints, (int)(tab.size() - head));
+    }
+    off[cs] = (int32_t)tab.size();
+    T.tab = upload(h, tab);
+    T.off = upload(h, off);
+}
+void build_tail_tables(smg_hierarchy* h, const Plan& P, int cs) {
+    for (int l = 0; l < h->H; l++)
+        for (int prec = 0; prec < 2; prec++) build_tail_table(h, P.L[l], h->L[l], cs, prec);
 }
 
 // Tail views of every level for one precision and a tail that starts at level
@@ -503,8 +518,10 @@ template <typename T>
 std::vector<TailLevel<T>> tail_table(smg_hierarchy* h, int t, int& dbase) {
     std::vector<TailLevel<T>> tab(h->H);
     const int cs = std::max(h->tail_cluster, 8);
-    int64_t budget = (int64_t)kTailSmemMax - (h->tail_cluster ? tail_slots(h, t) * (int64_t)sizeof(T) : 0);
-    for (int l = t; l < h->H; l++) budget -= ((h->L[l].ttab_ints * 4 + 15) / 16) * 16;
+    const bool single = sizeof(T) == 4;
+    const int prec = single ? 1 : 0;
+    int64_t budget = (int64_t)kTailSmemMax - (h->tail_cluster ? tail_slots(h, t, single) * (int64_t)sizeof(T) : 0);
+    for (int l = t; l < h->H; l++) budget -= ((h->L[l].tt[prec].ints * 4 + 15) / 16) * 16;
     int64_t sbase = 0, rbase = 0;
     for (int l = h->H - 1; l >= 0; l--) {
         DLevel& L = h->L[l];
@@ -518,22 +535,23 @@ std::vector<TailLevel<T>> tail_table(smg_hierarchy* h, int t, int& dbase) {
         e.dinv = v.dinv;
         e.diag = v.diag;
         e.colour_row = L.colour_row_dev;
-        e.table = L.ttab;
-        e.table_off = L.ttab_off;
+        e.table = L.tt[prec].tab;
+        e.table_off = L.tt[prec].off;
         e.x = v.x;
         e.b = v.b;
         e.nslices = L.nslices;
         e.ncolours = L.ncolours;
         e.n = (int)L.n;
-        e.rlg = L.maxw <= 32 ? 3 : L.maxw <= 64 ? 4 : 5;  // 4 entries per lane in registers
+        e.rlg = L.tt[prec].rlg;
         e.nloc = tail_nloc(L.n, cs);
         e.npad = tail_npad(L.n);
-        e.nwork = tail_nwork(L);
+        e.nwork = tail_nwork(L, single);
         e.sbase = (int)sbase;
         sbase += e.npad + 2 * (int64_t)e.nloc + e.nwork;
         int stage = 0;
-        for (const auto& en : L.t_E_nmy) stage = std::max(stage, StageLayout<T>(en.first, en.second).bytes);
-        e.tbytes = ((L.ttab_ints * 4 + 15) / 16) * 16;
+        for (const auto& en : L.tt[prec].E_nmy)
+            stage = std::max(stage, StageLayout<T>(en.first, en.second << (5 - L.tt[prec].rlg)).bytes);
+        e.tbytes = ((L.tt[prec].ints * 4 + 15) / 16) * 16;
         e.staged = (l >= t && stage <= budget) ? 1 : 0;
         if (e.staged) budget -= stage;
         e.rbase = (int)rbase;
@@ -589,10 +607,10 @@ int detect_tail_cluster() {
               allow_wide_clusters<float, 4>();
     cudaGetLastError();
     if (!ok) return 0;  // the tail kernels cannot get their shared memory: no tail
-    for (int cs : {16, 8}) {
+    auto fits = [](auto kernel, int cs, int threads) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs);
-        cfg.blockDim = dim3(kern::kTailThreads);
+        cfg.blockDim = dim3(threads);
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = cs;
@@ -601,11 +619,14 @@ int detect_tail_cluster() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, kern::tail_down<double, 4>, &cfg) == cudaSuccess && n >= 1 &&
-            cudaOccupancyMaxActiveClusters(&n, kern::tail_up<float, 1>, &cfg) == cudaSuccess && n >= 1)
-            return cs;
+        const bool ok = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) == cudaSuccess && n >= 1;
         cudaGetLastError();
-    }
+        return ok;
+    };
+    for (int cs : {16, 8})  // each kernel at its own block size (the largest register and thread demands)
+        if (fits(kern::tail_down<double, 4>, cs, kern::TailThreads<double>::value) &&
+            fits(kern::tail_down<float, 4>, cs, kern::TailThreads<float>::value))
+            return cs;
     return 0;
 }
 
@@ -653,11 +674,12 @@ void choose_tail(smg_hierarchy* h, bool tune) {
         int bestT = h->H;
         for (int cand = h->H - 1; cand >= 0 && h->L[cand].n <= 300000; cand--) {
             t = cand;
+            if (tail_start(h, prec == 1, 1) != cand) break;  // does not fit in one CTA's shared memory
             const float ms = time_cycle(h, prec == 1, e0, e1);
             if (trace)
                 std::fprintf(stderr, "[smg tune] %s cycle, tail from level %d: %.1f us\n", prec ? "f32" : "f64", cand,
                              ms * 1e3f);
-            if (ms < best * 0.97f) {
+            if (ms < best * 0.985f) {  // a larger tail must win by more than the timing noise
                 best = ms;
                 bestT = cand;
             }

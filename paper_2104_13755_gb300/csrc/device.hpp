@@ -36,11 +36,14 @@ struct DLevel {
     int32_t* colour_row_dev = nullptr;
     int maxw = 0;  // widest slice (off-diagonal entries per row)
     std::vector<int32_t> colour_slice;  // host copy, ncolours + 1
-    // cluster tail: per-CTA slice tables (see TailLevel) and their sizes
-    int32_t* ttab = nullptr;
-    int32_t* ttab_off = nullptr;
-    int ttab_ints = 0;                      // largest per-CTA table
-    std::vector<std::pair<int, int>> t_E_nmy;  // per CTA: staged entries, slices
+    // cluster tail: per-CTA work-unit tables (see TailLevel), binary64 and binary32
+    struct TailTable {
+        int32_t* tab = nullptr;
+        int32_t* off = nullptr;
+        int ints = 0;                              // largest per-CTA table
+        int rlg = 0;                               // log2 lanes per row
+        std::vector<std::pair<int, int>> E_nmy;    // per CTA: staged entries, units
+    } tt[2];
     SliceMeta* slices = nullptr;
     int32_t* sell_col = nullptr;
     double* vals = nullptr;  // flat A_l

@@ -89,7 +89,11 @@ struct RowSlice {
             if (sub + R * u < W)
 #pragma unroll
                 for (int q = 0; q < K; q++) xv[u][q] = ldx<COHERENT>(x + (int64_t)c[u] * K + q);
-        T a1[K];  // two independent FMA chains (binary64 FMAs are long-latency here)
+        // With several lanes per row (latency-bound levels) two independent FMA
+        // chains shorten the dependent binary64 chain; with one lane per row
+        // (the finest level, bound by FP64 issue) one chain saves the extra add.
+        constexpr bool SPLIT = R > 1;
+        T a1[K];
 #pragma unroll
         for (int q = 0; q < K; q++) acc[q] = a1[q] = T(0);
 #pragma unroll
@@ -97,7 +101,7 @@ struct RowSlice {
             if (sub + R * u < W)
 #pragma unroll
                 for (int q = 0; q < K; q++) {
-                    if (u & 1) a1[q] -= v[u] * xv[u][q];
+                    if (SPLIT && (u & 1)) a1[q] -= v[u] * xv[u][q];
                     else acc[q] -= v[u] * xv[u][q];
                 }
         for (int k = sub + R * PRE; k < W; k += R) {  // rows longer than PRE * R: the rare tail
@@ -106,8 +110,9 @@ struct RowSlice {
 #pragma unroll
             for (int q = 0; q < K; q++) acc[q] -= vv * ldx<COHERENT>(x + (int64_t)cc * K + q);
         }
+        if (SPLIT)
 #pragma unroll
-        for (int q = 0; q < K; q++) acc[q] += a1[q];
+            for (int q = 0; q < K; q++) acc[q] += a1[q];
 #pragma unroll
         for (int o = 16; o >= RL; o >>= 1)
 #pragma unroll

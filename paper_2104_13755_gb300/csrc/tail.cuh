@@ -7,17 +7,19 @@
 //
 // Every CTA keeps a full replica of each tail level's iterate x in its shared
 // memory, so the gathers of a colour step are local shared-memory loads; a
-// row's new value is written into all replicas (st.shared::cluster, spread over
-// the row's lanes) and colour classes are separated by the cluster barrier.
-// Remote shared-memory loads are an order of magnitude slower than local ones
-// in throughput, which is why x is replicated rather than distributed.  The
-// right-hand side b and the residual r are distributed: row i belongs to CTA
-// (i / 32) mod CS at local slot (i / (32 CS)) * 32 + i mod 32.  Each warp loads
-// the matrix entries, diagonal and right-hand side of its next colour step
-// between the arrive and the wait of the barrier ahead of it; where they fit,
-// a CTA's matrix entries are staged in shared memory at kernel entry.  Global
-// copies of x and b are read at entry and written at exit (the coarsest solve
-// and the full-GPU levels run between the two launches).
+// row's new value is written into all replicas with st.async (spread over the
+// row's lanes) and counted on the receivers' step mbarriers.  Remote
+// shared-memory loads have a small fraction of the throughput of local ones,
+// which is why x is replicated rather than distributed.  The right-hand side b
+// and the residual r are distributed: row i belongs to CTA (i / 32) mod CS at
+// local slot (i / (32 CS)) * 32 + i mod 32.  The work of a colour step is split
+// into warp-sized units (a slice's rows in groups of 32 / R, R lanes per row)
+// dealt round-robin over all CTAs, because binary64 issue, not memory, bounds a
+// step here.  Each warp loads the matrix entries, diagonal and right-hand side
+// of its next step before waiting for the current one; where they fit, a CTA's
+// units are staged in shared memory at kernel entry.  Global copies of x and b
+// are read at entry and written at exit (the coarsest solve and the full-GPU
+// levels run between the two launches).
 #pragma once
 
 #include "kernels.cuh"
@@ -26,16 +28,16 @@ namespace smg {
 
 // Device view of one level for the tail kernels (one precision).
 //
-// Each CTA works on the slices whose first row lies in one of its 32-row blocks
-// (a class's slices start 32 rows apart, so they rotate over the CTAs).  The
-// host writes, per CTA, a table of those slices, which the kernels copy to
+// The host deals each colour's work units (slice, row group g) round-robin over
+// the CTAs and writes, per CTA, a table of its units, which the kernels copy to
 // shared memory at entry:
-//   [n_my, E] [cfirst: ncolours + 1] [rows: ncolours] [n_my x {off, W, row0, nrows, soff}]
-// (cfirst[c] = index of the CTA's first slice of colour c, rows[c] = rows of colour c
-// in the level, E = sum W * 32, soff =
-// the slice's first entry in the staged copy).  When the level is staged, the
-// CTA also copies its slices' column indices, values, reciprocal diagonal and
-// diagonal to shared memory, so a colour step touches global memory not at all.
+//   [n_my, E] [cfirst: ncolours + 1] [rows: ncolours] [n_my x {off, W, row0, nrows, soff, g}]
+// (cfirst[c] = index of the CTA's first unit of colour c, rows[c] = rows of
+// colour c in the level, off = the slice's SELL offset, row0 / nrows = the
+// unit's rows, E = sum W * 32 / R, soff = the unit's first entry in the staged
+// copy).  When the level is staged, the CTA also copies its units' column
+// indices, values, reciprocal diagonal and diagonal to shared memory, so a
+// colour step touches global memory not at all.
 template <typename T>
 struct TailLevel {
     const SliceMeta* slices;
@@ -49,10 +51,10 @@ struct TailLevel {
     T* x;                         // global copies (entry and exit)
     T* b;
     int nslices, ncolours, n;
-    int rlg;                      // log2 of the lanes per row (8, 16 or 32: 4 entries per lane cover the longest row)
+    int rlg;                      // log2 of the lanes per row R (kTailPre entries per lane cover the longest row)
     int nloc;                     // distributed slots per CTA (multiple of 32)
     int npad;                     // replica slots of x (n rounded up to 32)
-    int nwork;                    // slots of the local copy of b for this CTA's rows (32 per slice, max over CTAs)
+    int nwork;                    // slots of the local copy of b for this CTA's rows (32 per unit, max over CTAs)
     int sbase;                    // first slot of this level's arrays: x replica at sbase, b at +npad, r at
                                   // +npad+nloc, local b at +npad+2 nloc
     int staged;                   // matrix entries copied to shared memory
@@ -65,30 +67,36 @@ struct TailLevel {
     int n_next;
     T* b_next;                    // global arrays of level + 1 (used when it is outside the tail)
     T* x_next;
-    int* err;                     // set when a wait for staged entries times out
+    int* err;                     // set when a step barrier wait times out
     // prolongation from level + 1
     const int32_t* p_idx;
     const T* p_w;
 };
 
-// Byte layout of a staged copy of E entries over n_my slices (value type T).
+// Byte layout of a staged copy of E entries over n_rows unit rows (value type T).
 template <typename T>
 struct StageLayout {
     int col, val, dinv, diag, bytes;
-    __host__ __device__ StageLayout(int E, int n_my) {
+    __host__ __device__ StageLayout(int E, int n_rows) {  // n_rows = units x rows per unit
         col = 0;
         val = ((E * 4 + 15) / 16) * 16;
         dinv = val + ((E * (int)sizeof(T) + 15) / 16) * 16;
-        diag = dinv + ((n_my * 32 * (int)sizeof(T) + 15) / 16) * 16;
-        bytes = diag + ((n_my * 32 * (int)sizeof(T) + 15) / 16) * 16;
+        diag = dinv + ((n_rows * (int)sizeof(T) + 15) / 16) * 16;
+        bytes = diag + ((n_rows * (int)sizeof(T) + 15) / 16) * 16;
     }
 };
 
 namespace kern {
 
-constexpr int kTailThreads = 512;
-constexpr int kTailWarps = kTailThreads / 32;
-constexpr int kTailPre = 4;  // entries per lane held in registers
+// Threads per CTA: binary64 steps are bound by FP64 issue, and eight warps
+// cover a colour's units at the tail sizes; binary32 steps are latency-bound
+// and use more, narrower units.
+template <typename T>
+struct TailThreads {
+    static constexpr int value = sizeof(T) == 8 ? 256 : 512;
+    static constexpr int warps = value / 32;
+};
+constexpr int kTailPre = 8;  // entries per lane held in registers
 
 // Split cluster barrier.  The release at arrive covers this thread's earlier
 // stores; loads of data that the phase does not write (matrix entries, b) may
@@ -199,14 +207,15 @@ struct Dist {
 template <typename T>
 struct LevelCtx {
     const TailLevel<T>* L;
-    uint32_t tab;  // [n_my, E, cfirst[nc + 1], rows[nc], 5 * n_my]
+    uint32_t tab;  // [n_my, E, cfirst[nc + 1], rows[nc], 6 * n_my]
     int n_my, nc, rlg, staged;
     uint32_t scol, sval, sdinv, sdiag;
-    uint32_t bw;  // local copy of b (32 rows per slice)
+    uint32_t bw;  // local copy of b (32 / R rows per unit)
     __device__ __forceinline__ int cfirst(int c) const { return lds_i(tab + 4u * (2 + c)); }
     __device__ __forceinline__ int rows(int c) const { return lds_i(tab + 4u * (3 + nc + c)); }
-    // field f of slice i: 0 off, 1 W, 2 row0, 3 nrows, 4 soff
-    __device__ __forceinline__ int slice(int i, int f) const { return lds_i(tab + 4u * (3 + 2 * nc + 5 * i + f)); }
+    // field f of work unit i: 0 SELL offset of its slice, 1 W, 2 first row, 3 rows, 4 staged offset,
+    // 5 row group g within the slice (rows g * 32 / R ...)
+    __device__ __forceinline__ int unit(int i, int f) const { return lds_i(tab + 4u * (3 + 2 * nc + 6 * i + f)); }
 };
 
 // mbarrier and bulk-copy helpers (shared::cta addresses).
@@ -214,31 +223,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-// Wait for phase `parity` of the mbarrier; gives up after a bounded number of
-// polls (the copies it waits for are a few hundred kilobytes at most) and
-// reports that through *err instead of hanging.
-__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-    if (err && *(volatile int*)err) return;  // an earlier wait gave up: do not wait again
-    for (int it = 0; it < (1 << 22); it++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return;
-    }
-    if (err) atomicExch(err, 1);
-}
-
 // A value into shared::cluster address a, counted on the mbarrier at cluster
 // address bar (in the CTA that owns a) as sizeof(value) completed bytes.
 __device__ __forceinline__ void st_async(uint32_t a, double v, uint32_t bar) {
@@ -290,12 +274,11 @@ struct StepBars {
 // local copy.  CTA-local, ends with __syncthreads.  `phase` counts the uses of
 // the mbarrier.
 template <typename T, int K>
-__device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const Dist& D, uint32_t bar,
-                                                   uint32_t& phase) {
+__device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const Dist& D) {
     const TailLevel<T>& L = *Lp;
     const uint32_t sm = (uint32_t)__cvta_generic_to_shared(tail_smem()) + (uint32_t)L.rbase;
     const int t0 = L.table_off[D.rank], t1 = L.table_off[D.rank + 1];
-    for (int e = threadIdx.x; e < t1 - t0; e += kTailThreads) sts_i(sm + 4u * e, L.table[t0 + e]);
+    for (int e = threadIdx.x; e < t1 - t0; e += TailThreads<T>::value) sts_i(sm + 4u * e, L.table[t0 + e]);
     __syncthreads();
     LevelCtx<T> C;
     C.L = Lp;
@@ -305,7 +288,7 @@ __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const
     C.nc = L.ncolours;
     C.rlg = L.rlg;
     C.staged = L.staged;
-    const StageLayout<T> lay(E, C.n_my);
+    const StageLayout<T> lay(E, C.n_my << (5 - C.rlg));
     const uint32_t st = sm + (uint32_t)L.tbytes;
     C.scol = st + lay.col;
     C.sval = st + lay.val;
@@ -313,32 +296,44 @@ __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const
     C.sdiag = st + lay.diag;
     C.bw = D.template rep<T, K>(L.sbase + L.npad + 2 * L.nloc, 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (C.staged && E > 0) {
-        if (threadIdx.x == 0) mbar_expect(bar, (uint32_t)E * (uint32_t)(4 + sizeof(T)));
-        __syncthreads();
-        for (int i = threadIdx.x; i < C.n_my; i += kTailThreads) {
-            const int off = C.slice(i, 0), W = C.slice(i, 1), soff = C.slice(i, 4);
-            if (W == 0) continue;  // rows without off-diagonal entries: nothing to copy
-            bulk_g2s(C.scol + 4u * soff, L.col + off, (uint32_t)W * 32u * 4u, bar);
-            bulk_g2s(C.sval + (uint32_t)sizeof(T) * soff, L.sval + off, (uint32_t)W * 32u * (uint32_t)sizeof(T), bar);
+    const int rl_lg = 5 - C.rlg, RL = 1 << rl_lg;  // rows per unit
+    for (int i = warp; i < C.n_my; i += TailThreads<T>::warps) {
+        const int off = C.unit(i, 0), W = C.unit(i, 1), row0 = C.unit(i, 2), nrows = C.unit(i, 3);
+        const int soff = C.unit(i, 4), g = C.unit(i, 5);
+        if (C.staged) {  // entries (k, rl) of the unit's rows, unit-major: staged index soff + k * RL + rl
+            const int n = W << rl_lg;
+            for (int e0 = 0; e0 < n; e0 += 32 * 4) {
+                int cv[4];
+                T vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int e = e0 + 32 * u + lane;
+                    if (e < n) {
+                        const int src = off + (e >> rl_lg) * 32 + g * RL + (e & (RL - 1));
+                        cv[u] = __ldg(L.col + src);
+                        vv[u] = __ldg(L.sval + src);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int e = e0 + 32 * u + lane;
+                    if (e < n) {
+                        sts_i(C.scol + 4u * (soff + e), cv[u]);
+                        sts(C.sval + (uint32_t)sizeof(T) * (soff + e), vv[u]);
+                    }
+                }
+            }
         }
-    }
-    for (int i = warp; i < C.n_my; i += kTailWarps) {
-        const int row0 = C.slice(i, 2), nrows = C.slice(i, 3);
         if (lane < nrows) {
             if (C.staged) {
-                sts(C.sdinv + (uint32_t)sizeof(T) * (32 * i + lane), L.dinv[row0 + lane]);
-                sts(C.sdiag + (uint32_t)sizeof(T) * (32 * i + lane), L.diag[row0 + lane]);
+                sts(C.sdinv + (uint32_t)sizeof(T) * ((i << rl_lg) + lane), L.dinv[row0 + lane]);
+                sts(C.sdiag + (uint32_t)sizeof(T) * ((i << rl_lg) + lane), L.diag[row0 + lane]);
             }
             const uint32_t src = D.template at<T, K>(L.sbase + L.npad, row0 + lane);
 #pragma unroll
             for (int q = 0; q < K; q++)
-                sts(C.bw + ((32 * i + lane) * K + q) * (int)sizeof(T), ldc<T>(src + q * (int)sizeof(T)));
+                sts(C.bw + (((i << rl_lg) + lane) * K + q) * (int)sizeof(T), ldc<T>(src + q * (int)sizeof(T)));
         }
-    }
-    if (C.staged && E > 0) {
-        mbar_wait(bar, phase & 1u, L.err);
-        phase++;
     }
     __syncthreads();
     return C;
@@ -355,33 +350,36 @@ struct TailRows {
     T d;
     uint32_t xrow;     // local replica address of this row's x (GS: offset for the broadcast)
     uint32_t rself;    // cluster address of this row's r (residual)
-    int base;          // first entry of the slice: staged offset (shared) or SELL offset (global)
+    int base;     // entry (k, r) of the unit is at base + k * rstride + r: staged (shared) or SELL (global)
+    int rstride;  // rows per unit when staged, 32 in the SELL arrays
     int W, r, sub, rlg;
     bool live, valid, staged;
 
     __device__ __forceinline__ int col_at(const LevelCtx<T>& C, int k) const {
-        const int e = base + k * 32 + r;
+        const int e = base + k * rstride + r;
         return staged ? lds_i(C.scol + 4u * e) : __ldg(C.L->col + e);
     }
     __device__ __forceinline__ T val_at(const LevelCtx<T>& C, int k) const {
-        const int e = base + k * 32 + r;
+        const int e = base + k * rstride + r;
         return staged ? lds<T>(C.sval + (uint32_t)sizeof(T) * e) : __ldg(C.L->sval + e);
     }
 
-    // my slice i (or none when i < 0), sub-slice g; RESIDUAL: diagonal, else its reciprocal
+    // work unit i (or none when i < 0); RESIDUAL: diagonal, else its reciprocal.
+    // Lane = sub * RL + r: entries k = sub, sub + R, ... of the unit's row r.
     template <bool RESIDUAL>
-    __device__ __forceinline__ void load(const LevelCtx<T>& C, const Dist& D, int i, int g, int lane) {
+    __device__ __forceinline__ void load(const LevelCtx<T>& C, const Dist& D, int i, int lane) {
         live = i >= 0;
         if (!live) return;
         const TailLevel<T>& L = *C.L;
         staged = C.staged != 0;
-        const int row0 = C.slice(i, 2), nrows = C.slice(i, 3);
-        W = C.slice(i, 1);
-        base = staged ? C.slice(i, 4) : C.slice(i, 0);
         rlg = C.rlg;
-        const int rl_lg = 5 - rlg;  // log2 rows per warp
+        const int rl_lg = 5 - rlg;  // log2 rows per unit
+        W = C.unit(i, 1);
+        const int row0 = C.unit(i, 2), nrows = C.unit(i, 3);
         sub = lane >> rl_lg;
-        r = (g << rl_lg) + (lane & ((1 << rl_lg) - 1));
+        r = lane & ((1 << rl_lg) - 1);
+        base = staged ? C.unit(i, 4) : C.unit(i, 0) + (C.unit(i, 5) << rl_lg);
+        rstride = staged ? (1 << rl_lg) : 32;
         valid = r < nrows;
         const int row = row0 + (valid ? r : 0);
 #pragma unroll
@@ -393,9 +391,9 @@ struct TailRows {
                 xa[u] = D.template rep<T, K>(L.sbase, c);
             }
         }
-        if (staged) d = lds<T>((RESIDUAL ? C.sdiag : C.sdinv) + (uint32_t)sizeof(T) * (32 * i + r));
+        if (staged) d = lds<T>((RESIDUAL ? C.sdiag : C.sdinv) + (uint32_t)sizeof(T) * ((i << rl_lg) + r));
         else d = RESIDUAL ? L.diag[row] : L.dinv[row];
-        const uint32_t ba = C.bw + (uint32_t)(((32 * i + r) * K) * (int)sizeof(T));
+        const uint32_t ba = C.bw + (uint32_t)((((i << rl_lg) + r) * K) * (int)sizeof(T));
 #pragma unroll
         for (int q = 0; q < K; q++) bb[q] = lds<T>(ba + q * (int)sizeof(T));
         xrow = D.template rep<T, K>(L.sbase, row);
@@ -468,19 +466,17 @@ template <typename T, int K, class ColourOf>
 __device__ __forceinline__ void tail_relax(const LevelCtx<T>& C, const Dist& D, int steps, ColourOf col_of,
                                            int warp, int lane, StepBars& sb) {
     TailRows<T, K> cur;
-    const int rlg = C.rlg;
     auto load = [&](int c, int u) {
-        const int m = u >> rlg;
-        const int i = C.cfirst(c) + m;
-        cur.template load<false>(C, D, i < C.cfirst(c + 1) ? i : -1, u & ((1 << rlg) - 1), lane);
+        const int i = C.cfirst(c) + u;
+        cur.template load<false>(C, D, i < C.cfirst(c + 1) ? i : -1, lane);
     };
     if (steps > 0) load(col_of(0), warp);
     for (int k = 0; k < steps; k++) {
         const int c = col_of(k);
-        const int units = (C.cfirst(c + 1) - C.cfirst(c)) << rlg;
+        const int units = C.cfirst(c + 1) - C.cfirst(c);
         const uint32_t bar = sb.bar();
         cur.template run<false>(C, D, bar);
-        for (int u = warp + kTailWarps; u < units; u += kTailWarps) {
+        for (int u = warp + TailThreads<T>::warps; u < units; u += TailThreads<T>::warps) {
             load(c, u);
             cur.template run<false>(C, D, bar);
         }
@@ -501,11 +497,9 @@ __device__ __forceinline__ void tail_relax(const LevelCtx<T>& C, const Dist& D, 
 // r = b - A x over all rows (this CTA's slices of every colour).
 template <typename T, int K>
 __device__ __forceinline__ void tail_residual(const LevelCtx<T>& C, const Dist& D, int warp, int lane) {
-    const int rlg = C.rlg;
-    const int units = C.n_my << rlg;
     TailRows<T, K> cur;
-    for (int u = warp; u < units; u += kTailWarps) {
-        cur.template load<true>(C, D, u >> rlg, u & ((1 << rlg) - 1), lane);
+    for (int u = warp; u < C.n_my; u += TailThreads<T>::warps) {
+        cur.template load<true>(C, D, u, lane);
         cur.template run<true>(C, D);
     }
 }
@@ -518,7 +512,7 @@ template <typename T, int K>
 __device__ __forceinline__ void tail_restrict(const TailLevel<T>& L, const TailLevel<T>* Ln, const Dist& D) {
     constexpr int RR = 4;
     const int sub = threadIdx.x % RR;
-    constexpr int per_pass = kTailThreads / RR;
+    constexpr int per_pass = TailThreads<T>::value / RR;
     const int nloc_next = ((L.n_next + (32 << D.lg) - 1) >> (5 + D.lg)) << 5;
     const int passes = (nloc_next + per_pass - 1) / per_pass;
     const int sr = L.sbase + L.npad + L.nloc;
@@ -557,7 +551,7 @@ __device__ __forceinline__ void tail_restrict(const TailLevel<T>& L, const TailL
         }
     }
     if (Ln)
-        for (int e = threadIdx.x; e < Ln->n * K; e += kTailThreads) sts(D.template rep<T, 1>(Ln->sbase * K, e), T(0));
+        for (int e = threadIdx.x; e < Ln->n * K; e += TailThreads<T>::value) sts(D.template rep<T, 1>(Ln->sbase * K, e), T(0));
 }
 
 // x_l += P x_{l+1} for the rows of level l this CTA owns, written to level l's
@@ -565,7 +559,7 @@ __device__ __forceinline__ void tail_restrict(const TailLevel<T>& L, const TailL
 // x_{l+1} from the local replica (Ln != nullptr) or from global memory.
 template <typename T, int K>
 __device__ __forceinline__ void tail_prolong(const TailLevel<T>& L, const TailLevel<T>* Ln, const Dist& D) {
-    for (int li = threadIdx.x; li < L.nloc; li += kTailThreads) {
+    for (int li = threadIdx.x; li < L.nloc; li += TailThreads<T>::value) {
         const int p = D.global(li);
         if (p >= L.n) continue;
         T acc[K];
@@ -593,14 +587,14 @@ __device__ __forceinline__ void tail_prolong(const TailLevel<T>& L, const TailLe
 // Global x of a level into this CTA's replica (all rows).
 template <typename T, int K>
 __device__ __forceinline__ void tail_load_x(const TailLevel<T>& L, const Dist& D) {
-    for (int e = threadIdx.x; e < L.n * K; e += kTailThreads) sts(D.template rep<T, 1>(L.sbase * K, e), L.x[e]);
+    for (int e = threadIdx.x; e < L.n * K; e += TailThreads<T>::value) sts(D.template rep<T, 1>(L.sbase * K, e), L.x[e]);
 }
 
 // This CTA's rows of b between global memory and the distributed array, and
 // (TO_SHARED = false) its rows of x from the replica to global memory.
 template <typename T, int K, bool TO_SHARED>
 __device__ __forceinline__ void tail_copy_own(const TailLevel<T>& L, const Dist& D, bool with_b) {
-    for (int e = threadIdx.x; e < L.nloc * K; e += kTailThreads) {
+    for (int e = threadIdx.x; e < L.nloc * K; e += TailThreads<T>::value) {
         const int li = e / K, q = e - li * K;
         const int i = D.global(li);
         if (i >= L.n) continue;
@@ -626,18 +620,16 @@ __device__ __forceinline__ Dist make_dist(int lg, int dbase) {
 // per-level arrays start at byte dbase of the dynamic shared memory, after the
 // slice tables and staged entries of the tail levels.
 template <typename T, int K>
-__global__ void __launch_bounds__(kTailThreads, 1) tail_down(const TailLevel<T>* __restrict__ lv, int l0, int l1,
+__global__ void __launch_bounds__(TailThreads<T>::value, 1) tail_down(const TailLevel<T>* __restrict__ lv, int l0, int l1,
                                                              int mu_pre, int lg, int dbase) {
     const Dist D = make_dist(lg, dbase);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ __align__(8) unsigned long long mbar[3];  // staging, even steps, odd steps
+    __shared__ __align__(8) unsigned long long mbar[2];  // step barriers: even, odd steps
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
-    uint32_t phase = 0;
-    StepBars sb{bar + 8u, 0u};
+    StepBars sb{bar, 0u};
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        mbar_init(bar, 1 << lg);
         mbar_init(bar + 8u, 1 << lg);
-        mbar_init(bar + 16u, 1 << lg);
     }
     pdl_wait();
     pdl_trigger();
@@ -645,7 +637,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_down(const TailLevel<T>*
     tail_copy_own<T, K, true>(lv[l0], D, true);
     cluster_sync();
     for (int l = l0; l < l1; l++) {
-        const LevelCtx<T> C = stage_level<T, K>(&lv[l], D, bar, phase);
+        const LevelCtx<T> C = stage_level<T, K>(&lv[l], D);
         const int nc = C.nc;
         tail_relax<T, K>(C, D, mu_pre * nc, [nc](int k) { return k % nc; }, warp, lane, sb);
         tail_residual<T, K>(C, D, warp, lane);
@@ -659,18 +651,16 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_down(const TailLevel<T>*
 // Up-sweep of levels [l0, l1) from level l1 - 1 upwards: prolongation with the
 // correction add, then post-relaxation (colour classes reversed if asked).
 template <typename T, int K>
-__global__ void __launch_bounds__(kTailThreads, 1) tail_up(const TailLevel<T>* __restrict__ lv, int l0, int l1,
+__global__ void __launch_bounds__(TailThreads<T>::value, 1) tail_up(const TailLevel<T>* __restrict__ lv, int l0, int l1,
                                                            int mu_post, int reverse, int lg, int dbase) {
     const Dist D = make_dist(lg, dbase);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ __align__(8) unsigned long long mbar[3];  // staging, even steps, odd steps
+    __shared__ __align__(8) unsigned long long mbar[2];  // step barriers: even, odd steps
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
-    uint32_t phase = 0;
-    StepBars sb{bar + 8u, 0u};
+    StepBars sb{bar, 0u};
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        mbar_init(bar, 1 << lg);
         mbar_init(bar + 8u, 1 << lg);
-        mbar_init(bar + 16u, 1 << lg);
     }
     pdl_wait();
     pdl_trigger();
@@ -683,7 +673,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_up(const TailLevel<T>* _
         tail_prolong<T, K>(lv[l], l + 1 < l1 ? &lv[l + 1] : nullptr, D);
         cluster_sync();  // level l's corrected x is in global memory
         tail_load_x<T, K>(lv[l], D);
-        const LevelCtx<T> C = stage_level<T, K>(&lv[l], D, bar, phase);
+        const LevelCtx<T> C = stage_level<T, K>(&lv[l], D);
         cluster_sync();  // every replica refreshed before any step writes into it
         const int nc = C.nc;
         tail_relax<T, K>(C, D, mu_post * nc, [nc, reverse](int k) { return reverse ? nc - 1 - k % nc : k % nc; },
