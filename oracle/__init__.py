@@ -525,3 +525,67 @@ def heat_loss(V, F, t, known, s):
     b[s] = m[s]
     x = spla.splu(A).solve(b)
     return float(m @ (x * x))
+
+
+# ---------------------------------------------------------------------------
+# The V-cycle as a preconditioner for conjugate gradients (Sec. "Limitations &
+# Future Work" names it as a direction; the paper gives no algorithm).
+# ---------------------------------------------------------------------------
+def _coldot(a, b):
+    return np.sum(a * b, axis=0)
+
+
+def pcg(levels, b, x0=None, opt=None, single=False, keep_iterates=False, trace=None, precond=True):
+    """Preconditioned conjugate gradients on A x = b, each column on its own.
+    The preconditioner is one V-cycle of Alg. 2 from a zero start with r as the
+    right-hand side (binary32 when `single`); with mu_pre = mu_post and the
+    post-relaxation in reverse colour order the cycle is a symmetric positive
+    definite operator.  `precond=False` gives plain CG (identity).  Stops like
+    Alg. 1: while max over columns of ||r|| / ||b|| > rtol, r the recurrence
+    residual.  `trace`, if a list, receives (r, z, p) of every iteration."""
+    opt = opt or Options()
+    A = levels[0].A
+    b2 = np.ascontiguousarray(b, dtype=np.float64).reshape(b.shape[0], -1)
+    x = np.zeros_like(b2) if x0 is None else np.array(x0, dtype=np.float64, copy=True).reshape(b2.shape)
+    r = b2 - A @ x
+    bn = np.linalg.norm(b2, axis=0)
+
+    def rel(res):
+        rn = np.linalg.norm(res, axis=0)
+        return float(np.max(np.where(bn > 0, rn / np.where(bn > 0, bn, 1.0), rn)))
+
+    hist = [rel(r)]
+    its = []
+    k = 0
+    p = None
+    rho_old = None
+    while hist[-1] > opt.rtol and k < opt.max_cycles:
+        if not precond:
+            z = r.copy()
+        elif single:
+            r32 = r.astype(np.float32).reshape(b.shape)
+            z = vcycle(levels, 0, np.zeros_like(r32), r32, opt, single=True).astype(np.float64).reshape(b2.shape)
+        else:
+            z = vcycle(levels, 0, np.zeros_like(r).reshape(b.shape), np.ascontiguousarray(r.reshape(b.shape)),
+                       opt).reshape(b2.shape)
+        rho = _coldot(r, z)
+        if p is None:
+            p = z.copy()
+        else:
+            beta = np.where(rho_old != 0, rho / np.where(rho_old != 0, rho_old, 1.0), 0.0)
+            p = z + beta * p
+        q = A @ p
+        pq = _coldot(p, q)
+        alpha = np.where(pq != 0, rho / np.where(pq != 0, pq, 1.0), 0.0)
+        if trace is not None:
+            trace.append((r.copy(), z.copy(), p.copy()))
+        x = x + alpha * p
+        r = r - alpha * q
+        rho_old = rho
+        k += 1
+        hist.append(rel(r))
+        if keep_iterates:
+            its.append(x.reshape(b.shape).copy())
+        if not np.isfinite(hist[-1]):
+            break
+    return SolveResult(x=x.reshape(b.shape), cycles=k, history=hist, iterates=its)
