@@ -230,8 +230,8 @@ def run_ours(args, w, rank, world, local_rank):
         h.update_positions(Vd, w["t"])
         h.solve_async(bd, xd)
 
-    def timed_steps(k, precision):
-        h.set_options(rtol=w["rtol"], max_cycles=200, precision=precision)
+    def timed_steps(k, precision, solver=smg.VCYCLE):
+        h.set_options(rtol=w["rtol"], max_cycles=200, precision=precision, solver=solver)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         cycles = []
         for i in range(k):
@@ -293,6 +293,17 @@ def run_ours(args, w, rank, world, local_rank):
 
     # mixed precision form, same steps
     ms_mx, cyc_mx = timed_steps(args.steps, smg.MIXED)
+    # the cycle as a CG preconditioner (same steps; one cycle per CG iteration)
+    pcg = {}
+    for name, p in (("fp64", smg.FP64), ("mixed", smg.MIXED)):
+        h.set_options(rtol=w["rtol"], max_cycles=200, precision=p, solver=smg.PCG)
+        for _ in range(2):  # graph instantiation
+            step(p)
+            torch.cuda.synchronize()
+            h.solve_result()
+        ms_cg, it_cg = timed_steps(args.steps, p, smg.PCG)
+        pcg[name] = {"time_to_tol_ms": sum(ms_cg) / len(ms_cg), "iterations_per_solve": it_cg[0],
+                     "V-cycles/s": sum(it_cg) * world / (sum(ms_cg) / 1e3)}
     h.set_options(rtol=w["rtol"], max_cycles=200, precision=smg.FP64)
 
     # stage timings with CUDA events on this stream (L2 flushed before each)
@@ -381,6 +392,7 @@ def run_ours(args, w, rank, world, local_rank):
         "per_level_sweeps": per_level,
         "mixed": {"value": sum(cyc_mx) * world / (sum(ms_mx) / 1e3), "ms_per_step": sum(ms_mx) / len(ms_mx),
                   "refinement_steps_per_solve": cyc_mx[0]},
+        "pcg": pcg,
         "roofline": {"kernel": "gs_colour<double,1> level-0 sweep (all colour launches)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": captured_traffic(), "traffic_source": "ncu dram__bytes_read.sum + "

@@ -49,6 +49,13 @@ extern "C" {
 #define SMG_MIXED 1   /* binary32 V-cycles inside binary64 iterative refinement; the
                          residual, the update and the coarsest Cholesky stay binary64 */
 
+#define SMG_SOLVER_VCYCLE 0  /* Alg. 1: repeat V-cycles while the relative residual exceeds rtol */
+#define SMG_SOLVER_PCG    1  /* conjugate gradients preconditioned by one V-cycle from a zero start
+                                (Sec. "Limitations & Future Work"); the cycle is symmetric when
+                                mu_pre == mu_post and post_reverse = 1 (the defaults).  CG vectors
+                                and scalars are binary64; with SMG_MIXED the preconditioner cycle is
+                                binary32.  smg_info.cycles counts CG iterations (one cycle each). */
+
 typedef void *smg_stream;   /* a cudaStream_t */
 
 /*
@@ -61,6 +68,7 @@ typedef void *smg_stream;   /* a cudaStream_t */
  *   rtol         stop when max over right-hand sides of ||b - A x|| / ||b|| <= rtol
  *   post_reverse 1: post-relaxation visits the colour classes in reverse order
  *                (symmetric cycle); 0: same order as pre-relaxation
+ *   solver       SMG_SOLVER_VCYCLE (default) or SMG_SOLVER_PCG
  *   autotune     1: smg_create times the smoother kernels of every level with
  *                1, 2, 4, 8 and 16 lanes per matrix row and keeps the fastest,
  *                then times whole cycles to choose the first level of the
@@ -79,6 +87,7 @@ typedef struct smg_options {
     int32_t precision;     /* SMG_FP64 or SMG_MIXED */
     int32_t post_reverse;
     int32_t autotune;
+    int32_t solver;        /* SMG_SOLVER_VCYCLE or SMG_SOLVER_PCG */
 } smg_options;
 
 /* Result of one solve (host struct filled by smg_solve). */

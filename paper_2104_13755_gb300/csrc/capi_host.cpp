@@ -15,7 +15,7 @@ using namespace smg;
 namespace {
 // ---------------------------------------------------------------- save / load
 const char kMagic[8] = {'S', 'M', 'G', 'P', 'L', 'A', 'N', '1'};
-const int32_t kVersion = 2;
+const int32_t kVersion = 3;  // 3: smg_options gained `solver`
 
 template <class T>
 bool wvec(FILE* f, const std::vector<T>& v) {
@@ -47,6 +47,7 @@ void smg_default_options(smg_options* o) {
     o->precision = SMG_FP64;
     o->post_reverse = 1;
     o->autotune = 1;
+    o->solver = SMG_SOLVER_VCYCLE;
 }
 
 const char* smg_status_string(int s) {

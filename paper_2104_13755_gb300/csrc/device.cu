@@ -212,7 +212,7 @@ void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
 // Level-0 residual norm partials (binary64); with r32 also the binary32 residual
 // (next inner right-hand side) and a zero binary32 iterate.
 template <int K>
-void rec_resnorm(smg_hierarchy* h, bool init, bool r32, cudaStream_t s) {
+void rec_resnorm(smg_hierarchy* h, bool init, bool r32, cudaStream_t s, double* r64 = nullptr) {
     DLevel& L = h->L[0];
     float* out32 = L.b32;
     float* x32 = L.x32;
@@ -222,7 +222,7 @@ void rec_resnorm(smg_hierarchy* h, bool init, bool r32, cudaStream_t s) {
     const double* vals = L.vals;
     if (L.coarsest) {
         const int n = (int)L.n;
-#define SMG_RN(I, R32) ck(launch_pdl(kern::resnorm_dense<K, I, R32>, grid, block, s, n, vals, b, x, h->partials, out32, x32), "resnorm")
+#define SMG_RN(I, R32) ck(launch_pdl(kern::resnorm_dense<K, I, R32>, grid, block, s, n, vals, b, x, h->partials, out32, x32, r64), "resnorm")
         if (init && r32) SMG_RN(true, true);
         else if (init) SMG_RN(true, false);
         else if (r32) SMG_RN(false, true);
@@ -235,7 +235,7 @@ void rec_resnorm(smg_hierarchy* h, bool init, bool r32, cudaStream_t s) {
     const double* sval = L.vals + L.sbase;
 #define SMG_RN(I, R32)                                                                                            \
     SMG_R_SWITCH(L.R, ck(launch_pdl(kern::resnorm<K, RR, I, R32>, grid, block, s, sl, L.nslices, col, sval, vals, b, \
-                                    x, h->partials, out32, x32), "resnorm"))
+                                    x, h->partials, out32, x32, r64), "resnorm"))
     if (init && r32) SMG_RN(true, true);
     else if (init) SMG_RN(true, false);
     else if (r32) SMG_RN(false, true);
@@ -272,6 +272,48 @@ void rec_final(smg_hierarchy* h, cudaGraphConditionalHandle hnd, bool init, bool
        "norm final");
 }
 
+// One iteration of conjugate gradients preconditioned by one V-cycle (binary64,
+// or binary32 when `mixed`) from a zero start: z = cycle(r), beta, p, q = A p,
+// alpha, x and r, and the partials of ||r||^2 for the stopping test.
+template <typename T, int K>
+void rec_pcg_iteration(smg_hierarchy* h, cudaStream_t s) {
+    DLevel& L0 = h->L[0];
+    LevelView<T> v0 = view<T>(L0);
+    const int64_t n = L0.n, m = n * K;
+    const dim3 eg(blocks_for(m)), blk(kern::kThreads), rg(kern::kNormBlocks);
+    const double* r = h->cg_r;
+    ck(launch_pdl(kern::cg_precond_in<T>, eg, blk, s, m, r, v0.b, v0.x), "cg precond in");
+    if (h->H == 0) record_coarsest_solve(h, K, v0.b, sizeof(T) == 4, v0.x, sizeof(T) == 4, s);
+    else rec_vcycle<T, K>(h, s);
+    const T* z = v0.x;
+    ck(launch_pdl(kern::cg_dot<K, T>, rg, blk, s, n, r, z, h->part_rz), "cg dot");
+    const double* prz = h->part_rz;
+    ck(launch_pdl(kern::cg_p_update<K, T>, rg, blk, s, n, prz, z, h->cg_p, h->state), "cg p");
+    const double* p = h->cg_p;
+    if (L0.coarsest) {
+        ck(launch_pdl(kern::cg_spmv_dense<K>, rg, blk, s, (int)n, (const double*)L0.vals, p, h->cg_q, h->part_pq),
+           "cg spmv");
+    } else {
+        const SliceMeta* sl = L0.slices;
+        const int32_t* col = L0.sell_col;
+        const double* sval = L0.vals + L0.sbase;
+        const double* diag = L0.vals;
+        SMG_R_SWITCH(std::max(L0.R, 1), ck(launch_pdl(kern::cg_spmv<K, RR>, rg, blk, s, sl, L0.nslices, col, sval,
+                                                       diag, p, h->cg_q, h->part_pq),
+                                            "cg spmv"));
+    }
+    const double* ppq = h->part_pq;
+    const double* q = h->cg_q;
+    const SolveState* st = h->state;
+    ck(launch_pdl(kern::cg_xr_update<K>, rg, blk, s, n, ppq, p, q, h->cg_x, h->cg_r, st, h->partials), "cg x r");
+}
+
+template <int K>
+void rec_copy(smg_hierarchy* h, const double* src, double* dst, cudaStream_t s) {
+    const int64_t m = h->L[0].n * K;
+    ck(launch_pdl(kern::cg_copy, dim3(blocks_for(m)), dim3(kern::kThreads), s, m, src, dst), "copy");
+}
+
 // Append to graph g an independent branch solving one system: optional
 // prologue, ||b|| and the first stopping test, a WHILE node running one cycle
 // + residual norm + stopping test per iteration, optional epilogue after the
@@ -283,8 +325,14 @@ void add_solve_branch(smg_hierarchy* h, cudaGraph_t g, cudaStream_t s, bool mixe
     cudaGraphConditionalHandle hnd;
     ck(cudaGraphConditionalHandleCreate(&hnd, g, 0, 0), "cudaGraphConditionalHandleCreate");
     ck(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), "capture init");
+    const bool pcg = h->opts.solver == SMG_SOLVER_PCG;
     if (prologue) prologue(s);
-    rec_resnorm<K>(h, true, mixed, s);
+    if (pcg) {  // r = b - A x0 kept in binary64; the CG iterate leaves x_0 free for the preconditioner
+        rec_resnorm<K>(h, true, false, s, h->cg_r);
+        rec_copy<K>(h, h->L[0].x, h->cg_x, s);
+    } else {
+        rec_resnorm<K>(h, true, mixed, s);
+    }
     rec_final<K>(h, hnd, true, true, s);
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
@@ -303,15 +351,21 @@ void add_solve_branch(smg_hierarchy* h, cudaGraph_t g, cudaStream_t s, bool mixe
     ck(cudaGraphAddNode(&wnode, g, frontier.data(), nullptr, frontier.size(), &cp), "add while node");
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     ck(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), "capture body");
-    if (mixed) rec_cycle_mixed<K>(h, s);
-    else rec_cycle_fp64<K>(h, s);
-    rec_resnorm<K>(h, false, mixed, s);
+    if (pcg) {
+        if (mixed) rec_pcg_iteration<float, K>(h, s);
+        else rec_pcg_iteration<double, K>(h, s);
+    } else {
+        if (mixed) rec_cycle_mixed<K>(h, s);
+        else rec_cycle_fp64<K>(h, s);
+        rec_resnorm<K>(h, false, mixed, s);
+    }
     rec_final<K>(h, hnd, false, true, s);
     ck(cudaGetLastError(), "body launches");
     ck(cudaStreamEndCapture(s, &body), "end capture body");
-    if (epilogue) {
+    if (epilogue || pcg) {
         ck(cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal), "capture epilogue");
-        epilogue(s);
+        if (pcg) rec_copy<K>(h, h->cg_x, h->L[0].x, s);
+        if (epilogue) epilogue(s);
         ck(cudaGetLastError(), "epilogue launches");
         gg = g;
         ck(cudaStreamEndCapture(s, &gg), "end capture epilogue");
@@ -345,7 +399,7 @@ cudaGraphExec_t build_cycle_graph(smg_hierarchy* h, bool mixed) {
 }
 
 cudaGraphExec_t solve_graph(smg_hierarchy* h, int K, bool mixed) {
-    const int key = (mixed ? 16 : 0) + K;
+    const int key = (h->opts.solver == SMG_SOLVER_PCG ? 32 : 0) + (mixed ? 16 : 0) + K;
     auto it = h->solve_exec.find(key);
     if (it != h->solve_exec.end()) return it->second;
     cudaGraphExec_t e = nullptr;
@@ -842,6 +896,15 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
     h->state = dalloc<SolveState>(h, 1);
     ck(cudaMemset(h->state, 0, sizeof(SolveState)), "memset");
     h->partials = dalloc<double>(h, (int64_t)kern::kNormBlocks * 2 * kMaxRhs);
+    h->part_rz = dalloc<double>(h, (int64_t)kern::kNormBlocks * kMaxRhs);
+    h->part_pq = dalloc<double>(h, (int64_t)kern::kNormBlocks * kMaxRhs);
+    {
+        const int64_t m0 = P.L[0].n * kMaxRhs;
+        h->cg_x = dalloc<double>(h, m0);
+        h->cg_r = dalloc<double>(h, m0);
+        h->cg_p = dalloc<double>(h, m0);
+        h->cg_q = dalloc<double>(h, m0);
+    }
     ck(cudaMallocHost((void**)&h->state_host, sizeof(SolveState)), "cudaMallocHost");
     h->tail_cluster = detect_tail_cluster();
     if (h->H > 0) {
@@ -949,8 +1012,10 @@ int smg_create(const smg_plan* plan, const smg_options* opts, smg_hierarchy** ou
         o.precision = opts->precision;
         o.post_reverse = opts->post_reverse;
         o.autotune = opts->autotune;
+        o.solver = opts->solver;
     }
-    if (o.mu_pre < 0 || o.mu_post < 0 || o.max_cycles < 0 || !(o.rtol >= 0))
+    if (o.mu_pre < 0 || o.mu_post < 0 || o.max_cycles < 0 || !(o.rtol >= 0) ||
+        (o.solver != SMG_SOLVER_VCYCLE && o.solver != SMG_SOLVER_PCG))
         return fail("invalid solve options", SMG_ERR_INVALID_ARG);
     smg_hierarchy* h = new (std::nothrow) smg_hierarchy();
     if (!h) return SMG_ERR_NO_MEMORY;
@@ -991,7 +1056,8 @@ void smg_destroy(smg_hierarchy* h) {
 int smg_set_options(smg_hierarchy* h, const smg_options* o) {
     if (!h || !o) return fail("null argument", SMG_ERR_INVALID_ARG);
     if (o->mu_pre < 0 || o->mu_post < 0 || o->max_cycles < 0 || !(o->rtol >= 0) ||
-        (o->precision != SMG_FP64 && o->precision != SMG_MIXED))
+        (o->precision != SMG_FP64 && o->precision != SMG_MIXED) ||
+        (o->solver != SMG_SOLVER_VCYCLE && o->solver != SMG_SOLVER_PCG))
         return fail("invalid solve options", SMG_ERR_INVALID_ARG);
     h->opts.mu_pre = o->mu_pre;
     h->opts.mu_post = o->mu_post;
@@ -999,6 +1065,7 @@ int smg_set_options(smg_hierarchy* h, const smg_options* o) {
     h->opts.rtol = o->rtol;
     h->opts.precision = o->precision;
     h->opts.post_reverse = o->post_reverse;
+    h->opts.solver = o->solver;
     drop_graphs(h);
     return SMG_OK;
 }

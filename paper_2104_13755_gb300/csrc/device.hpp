@@ -23,7 +23,8 @@ struct SolveState {
     int32_t cycles;
     int32_t status;          // SMG_OK / SMG_ERR_NOT_CONVERGED / SMG_ERR_DIVERGED / -1 running
     int32_t chol_bad;        // nonzero: a coarsest pivot was not positive
-    int32_t tail_err;        // nonzero: a cluster-tail wait for staged matrix entries timed out
+    int32_t tail_err;        // nonzero: a cluster-tail step barrier wait timed out
+    double cg_rho[2][kMaxRhs];  // conjugate gradients: r . z of the last two iterations (slot = iteration & 1)
 };
 
 struct DLevel {
@@ -103,6 +104,10 @@ struct smg_hierarchy {
     smg::SolveState* state = nullptr;
     smg::SolveState* state_host = nullptr;  // pinned
     double* partials = nullptr;             // [kNormBlocks][2 * kMaxRhs]
+    // conjugate gradients (level-0 unknowns x kMaxRhs): iterate, residual, direction, A times direction,
+    // and the partials of r . z and p . A p
+    double *cg_x = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
+    double *part_rz = nullptr, *part_pq = nullptr;
     cudaStream_t cap = nullptr;             // private capture stream
     cudaStream_t aux = nullptr;             // second capture stream (parallel graph branch)
     std::vector<cudaEvent_t> ev_step;       // fork points of the coarsest factorisation

@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(kThreads) resnorm(const SliceMeta* __restrict_
                                                     const int32_t* __restrict__ col, const double* __restrict__ sval,
                                                     const double* __restrict__ diag, const double* __restrict__ b,
                                                     const double* __restrict__ x, double* __restrict__ partials,
-                                                    float* __restrict__ r32, float* __restrict__ x32) {
+                                                    float* __restrict__ r32, float* __restrict__ x32,
+                                                    double* __restrict__ r64) {
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     pdl_wait();
@@ -283,6 +284,7 @@ __global__ void __launch_bounds__(kThreads) resnorm(const SliceMeta* __restrict_
                 const double bv = b[(int64_t)row * K + q];
                 const double rv = (bv - d * x[(int64_t)row * K + q]) + acc[q];
                 rr[q] += rv * rv;
+                if (r64) r64[(int64_t)row * K + q] = rv;
                 if (INIT) bb[q] += bv * bv;
                 if (R32) {
                     r32[(int64_t)row * K + q] = (float)rv;
@@ -318,7 +320,7 @@ template <int K, bool INIT, bool R32>
 __global__ void __launch_bounds__(kThreads) resnorm_dense(int n, const double* __restrict__ A,
                                                           const double* __restrict__ b, const double* __restrict__ x,
                                                           double* __restrict__ partials, float* __restrict__ r32,
-                                                          float* __restrict__ x32) {
+                                                          float* __restrict__ x32, double* __restrict__ r64) {
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     pdl_wait();
@@ -342,6 +344,7 @@ __global__ void __launch_bounds__(kThreads) resnorm_dense(int n, const double* _
             const double rv = bv - acc[q];
             if (lane == 0) {
                 rr[q] += rv * rv;
+                if (r64) r64[(int64_t)i * K + q] = rv;
                 if (INIT) bb[q] += bv * bv;
                 if (R32) {
                     r32[(int64_t)i * K + q] = (float)rv;
@@ -410,6 +413,215 @@ __global__ void norm_final(const double* __restrict__ partials, int nblocks, Sol
     const bool more = finite && !converged && st->cycles < max_cycles;
     st->status = converged ? SMG_OK : (!finite ? SMG_ERR_DIVERGED : (more ? -1 : SMG_ERR_NOT_CONVERGED));
     if (use_cond) cudaGraphSetConditional(hnd, more ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Conjugate gradients preconditioned by one V-cycle from a zero start (Sec.
+// "Limitations & Future Work" names the multigrid cycle as a CG
+// preconditioner).  Each right-hand side is its own CG.  Every reduction uses
+// the fixed grid of kNormBlocks blocks and a fixed order, and the scalars
+// (alpha, beta) are recomputed identically by every block from the partials,
+// so the iteration is bitwise reproducible and needs no extra launches.
+
+// Sum of the K-column block partials (stride doubles per block) in a fixed
+// order; every thread of the block gets the totals.
+template <int K>
+__device__ __forceinline__ void sum_partials(const double* __restrict__ part, int nblocks, int stride,
+                                             double (&out)[K]) {
+    __shared__ double red[kThreads][K];
+    double acc[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) acc[q] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kThreads)
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] += part[(int64_t)b * stride + q];
+#pragma unroll
+    for (int q = 0; q < K; q++) red[threadIdx.x][q] = acc[q];
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < K; q++) red[threadIdx.x][q] += red[threadIdx.x + w][q];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) out[q] = red[0][q];
+    __syncthreads();
+}
+
+// Block reduction of per-thread column sums into part[block * stride + q].
+template <int K>
+__device__ __forceinline__ void block_partials(double (&v)[K], double* __restrict__ part, int stride) {
+    __shared__ double red[kWarps][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < K; q++)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < K; q++) red[wid][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; w++) t += red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * stride + threadIdx.x] = t;
+    }
+}
+
+__global__ void cg_copy(int64_t m, const double* __restrict__ src, double* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    pdl_wait();
+    pdl_trigger();
+    dst[e] = src[e];
+}
+
+// Right-hand side and zero start of the preconditioner cycle: b_0 <- r, x_0 <- 0.
+template <typename T>
+__global__ void cg_precond_in(int64_t m, const double* __restrict__ r, T* __restrict__ b0, T* __restrict__ x0) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    pdl_wait();
+    pdl_trigger();
+    b0[e] = (T)r[e];
+    x0[e] = T(0);
+}
+
+// Partials of rho = r . z per column (z in the cycle's precision).
+template <int K, typename TZ>
+__global__ void __launch_bounds__(kThreads) cg_dot(int64_t n, const double* __restrict__ r, const TZ* __restrict__ z,
+                                                   double* __restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
+    double acc[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) acc[q] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] += r[i * K + q] * (double)z[i * K + q];
+    block_partials<K>(acc, part, K);
+}
+
+// p <- z + beta p, beta = rho / rho_previous (p <- z in the first iteration).
+// rho goes to slot (iteration & 1) of the state; the previous one is read from
+// the other slot, so block 0's store cannot race the other blocks' loads.
+template <int K, typename TZ>
+__global__ void __launch_bounds__(kThreads) cg_p_update(int64_t n, const double* __restrict__ part_rz,
+                                                        const TZ* __restrict__ z, double* __restrict__ p,
+                                                        SolveState* __restrict__ st) {
+    pdl_wait();
+    pdl_trigger();
+    double rho[K];
+    sum_partials<K>(part_rz, kNormBlocks, K, rho);
+    const int it = st->cycles;
+    double beta[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        const double old = st->cg_rho[(it + 1) & 1][q];
+        beta[q] = (it == 0 || old == 0.0) ? 0.0 : rho[q] / old;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < K; q++) st->cg_rho[it & 1][q] = rho[q];
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const double zv = (double)z[i * K + q];
+            p[i * K + q] = it == 0 ? zv : zv + beta[q] * p[i * K + q];
+        }
+}
+
+// q <- A p and the partials of p . q (SELL level 0, diagonal apart).
+template <int K, int R>
+__global__ void __launch_bounds__(kThreads) cg_spmv(const SliceMeta* __restrict__ slices, int nslices,
+                                                    const int32_t* __restrict__ col, const double* __restrict__ sval,
+                                                    const double* __restrict__ diag, const double* __restrict__ p,
+                                                    double* __restrict__ qv, double* __restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    pdl_wait();
+    pdl_trigger();
+    double pq[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) pq[q] = 0.0;
+    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nslices * R; w += gridDim.x * kWarps) {
+        const SliceMeta m = slices[w / R];
+        RowSlice<double, K, R, Pre<double, K, R>::value> rs;
+        rs.load(m, w % R, lane, col, sval);
+        double acc[K];
+        rs.dot(m, col, sval, p, acc);  // acc = -(sum of the off-diagonal products)
+        if (rs.r < m.nrows && rs.sub == 0) {
+            const int row = m.row0 + rs.r;
+            const double d = diag[row];
+#pragma unroll
+            for (int q = 0; q < K; q++) {
+                const double pv = p[(int64_t)row * K + q];
+                const double v = d * pv - acc[q];
+                qv[(int64_t)row * K + q] = v;
+                pq[q] += pv * v;
+            }
+        }
+    }
+    block_partials<K>(pq, part, K);
+}
+
+// The same for a dense level-0 matrix (single-level hierarchy): a warp per row.
+template <int K>
+__global__ void __launch_bounds__(kThreads) cg_spmv_dense(int n, const double* __restrict__ A,
+                                                          const double* __restrict__ p, double* __restrict__ qv,
+                                                          double* __restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    pdl_wait();
+    pdl_trigger();
+    double pq[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) pq[q] = 0.0;
+    for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += gridDim.x * kWarps) {
+        double acc[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] = 0.0;
+        for (int j = lane; j < n; j += 32)
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[q] += A[(int64_t)i * n + j] * p[(int64_t)j * K + q];
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (lane == 0) {
+                qv[(int64_t)i * K + q] = acc[q];
+                pq[q] += p[(int64_t)i * K + q] * acc[q];
+            }
+        }
+    }
+    block_partials<K>(pq, part, K);
+}
+
+// x <- x + alpha p, r <- r - alpha q with alpha = rho / (p . q), and the
+// partials of ||r||^2 in the layout of the stopping test (2K per block).
+template <int K>
+__global__ void __launch_bounds__(kThreads) cg_xr_update(int64_t n, const double* __restrict__ part_pq,
+                                                         const double* __restrict__ p, const double* __restrict__ qv,
+                                                         double* __restrict__ x, double* __restrict__ r,
+                                                         const SolveState* __restrict__ st, double* __restrict__ part_rr) {
+    pdl_wait();
+    pdl_trigger();
+    double pq[K];
+    sum_partials<K>(part_pq, kNormBlocks, K, pq);
+    const int it = st->cycles;
+    double alpha[K], rr[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        alpha[q] = pq[q] != 0.0 ? st->cg_rho[it & 1][q] / pq[q] : 0.0;
+        rr[q] = 0.0;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            x[i * K + q] += alpha[q] * p[i * K + q];
+            const double rv = r[i * K + q] - alpha[q] * qv[i * K + q];
+            r[i * K + q] = rv;
+            rr[q] += rv * rv;
+        }
+    block_partials<K>(rr, part_rr, 2 * K);
+    if (threadIdx.x < K) part_rr[(int64_t)blockIdx.x * 2 * K + K + threadIdx.x] = 0.0;
 }
 
 // ---------------------------------------------------------------------------
