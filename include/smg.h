@@ -180,8 +180,8 @@ int  smg_setup(const double *V, int64_t n, const int32_t *F, int64_t m,
                const uint8_t *dirichlet_mask, const smg_options *opts, smg_hierarchy **out);
 void smg_destroy(smg_hierarchy *h);
 
-/* Replace rtol / max_cycles / precision / mu / post_reverse for later solves
- * (decimation fields are ignored). */
+/* Replace rtol / max_cycles / precision / mu / post_reverse / solver for later
+ * solves (decimation fields are ignored). */
 int  smg_set_options(smg_hierarchy *h, const smg_options *opts);
 
 /*
@@ -192,7 +192,12 @@ int  smg_set_options(smg_hierarchy *h, const smg_options *opts);
  *                         numbering as setup); assembles A = M + t L with the
  *                         cotangent Laplacian L (positive semi-definite sign)
  *                         and the barycentric lumped mass M.
- *   smg_update_t          same with the last positions and a new t.
+ *   smg_update_t          same with the last positions and a new t.  Uses the
+ *                         split of App. "Fast Data Smoothing": the first call
+ *                         after new positions computes P^T L P and P^T M P of
+ *                         every level (device memory: two more value arrays per
+ *                         level); every call then forms A_l = P^T M P + t P^T L P
+ *                         with one pass per level and refactors the coarsest.
  *   smg_update_matrix     vals_dev: user-supplied A on the level-0 pattern
  *                         (smg_plan_pattern level 0, nnz values); must be
  *                         symmetric positive definite.

@@ -761,6 +761,54 @@ void rec_update(smg_hierarchy* h, cudaStream_t s) {
     record_coarsest_factor(h, s);
 }
 
+// Galerkin products of L and M on their own, down the hierarchy (App. "Fast
+// Data Smoothing": P^T A P = P^T M P + t P^T L P), computed once per positions.
+void ensure_split(smg_hierarchy* h, cudaStream_t s) {
+    if (h->split_valid) return;
+    DLevel& L0 = h->L[0];
+    if (!L0.Mg) {
+        L0.Lg = h->Lflat0;
+        L0.Mg = dalloc<double>(h, L0.nflat);
+        for (int l = 1; l <= h->H; l++) {
+            h->L[l].Lg = dalloc<double>(h, h->L[l].nflat);
+            h->L[l].Mg = dalloc<double>(h, h->L[l].nflat);
+        }
+    }
+    kern::mass_flat<<<blocks_for(L0.nflat), kern::kThreads, 0, s>>>(L0.nflat, L0.n, L0.coarsest ? L0.n : 0, h->Mdiag,
+                                                                   L0.Mg);
+    for (int l = 0; l < h->H; l++) {
+        DLevel& L = h->L[l];
+        DLevel& N = h->L[l + 1];
+        kern::galerkin<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_w, L.Lg, N.Lg);
+        kern::galerkin<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_w, L.Mg, N.Mg);
+    }
+    ck(cudaGetLastError(), "split launches");
+    h->split_valid = true;
+}
+
+// Every level's A = M + t L from the kept products (t in h->t_fast), the level
+// preparation and the coarsest factor, as one graph.
+void build_fast_t_graph(smg_hierarchy* h) {
+    cudaStream_t s = h->cap;
+    cudaGraph_t g = nullptr;
+    ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture fast t");
+    ck(cudaMemsetAsync(&h->state->chol_bad, 0, sizeof(int32_t), s), "memset");
+    for (int l = 0; l <= h->H; l++) {
+        DLevel& L = h->L[l];
+        kern::axpy_devt<<<blocks_for(L.nflat), kern::kThreads, 0, s>>>(L.nflat, h->t_fast, L.Lg, L.Mg, L.vals);
+    }
+    for (int l = 0; l < h->H; l++) {
+        DLevel& L = h->L[l];
+        kern::prep_level<<<blocks_for(L.nflat), kern::kThreads, 0, s>>>(L.nflat, L.n, L.vals, L.dinv, L.vals32,
+                                                                      L.dinv32);
+    }
+    record_coarsest_factor(h, s);
+    ck(cudaGetLastError(), "fast t launches");
+    ck(cudaStreamEndCapture(s, &g), "end capture fast t");
+    ck(cudaGraphInstantiate(&h->fast_t_exec, g, 0), "instantiate fast t graph");
+    cudaGraphDestroy(g);
+}
+
 // Level-0 assembly A = M + t L from positions V (t from device memory).
 void rec_assembly(smg_hierarchy* h, const double* V, const double* t_dev, cudaStream_t s) {
     DLevel& L0 = h->L[0];
@@ -796,6 +844,7 @@ void drop_graphs(smg_hierarchy* h) {
 void free_all(smg_hierarchy* h) {
     drop_graphs(h);
     if (h->update_exec) cudaGraphExecDestroy(h->update_exec);
+    if (h->fast_t_exec) cudaGraphExecDestroy(h->fast_t_exec);
     for (void* p : h->allocs) cudaFree(p);
     if (h->state_host) cudaFreeHost(h->state_host);
     for (auto e : h->ev_step)
@@ -1088,6 +1137,7 @@ int smg_update_positions(smg_hierarchy* h, const double* V, double t, smg_stream
     ck(cudaGetLastError(), "assembly launches");
     ck(cudaGraphLaunch(h->update_exec, s), "update graph");
     h->have_positions = h->have_matrix = true;
+    h->split_valid = false;
     return SMG_OK;
     SMG_GUARD_END
 }
@@ -1097,11 +1147,14 @@ int smg_update_t(smg_hierarchy* h, double t, smg_stream stream) {
     if (!h->have_positions) return fail("smg_update_t needs a previous smg_update_positions", SMG_ERR_STATE);
     cudaStream_t s = (cudaStream_t)stream;
     SMG_GUARD_BEGIN
-    DLevel& L0 = h->L[0];
-    kern::combine<<<blocks_for(L0.nflat), kern::kThreads, 0, s>>>(L0.nflat, L0.n, L0.coarsest ? L0.n : 0, t, h->Lflat0,
-                                                                  h->Mdiag, L0.vals);
-    ck(cudaGetLastError(), "combine launch");
-    ck(cudaGraphLaunch(h->update_exec, s), "update graph");
+    // App. "Fast Data Smoothing": the first call after new positions keeps P^T L P
+    // and P^T M P of every level; every call then only combines them with t
+    if (!h->t_fast) h->t_fast = dalloc<double>(h, 1);
+    ensure_split(h, s);
+    if (!h->fast_t_exec) build_fast_t_graph(h);
+    kern::set_scalar<<<1, 1, 0, s>>>(h->t_fast, t);
+    ck(cudaGetLastError(), "set t");
+    ck(cudaGraphLaunch(h->fast_t_exec, s), "fast t graph");
     h->have_matrix = true;
     return SMG_OK;
     SMG_GUARD_END
@@ -1367,7 +1420,10 @@ int smg_batch_update_positions(smg_batch* B, const double* V, double t, smg_stre
     *B->t_host = t;
     ck(cudaMemcpyAsync(B->t_dev, B->t_host, sizeof(double), cudaMemcpyHostToDevice, s), "copy t");
     ck(cudaGraphLaunch(B->update_exec, s), "batch update");
-    for (smg_hierarchy* h : B->hs) h->have_positions = h->have_matrix = true;
+    for (smg_hierarchy* h : B->hs) {
+        h->have_positions = h->have_matrix = true;
+        h->split_valid = false;
+    }
     return SMG_OK;
     SMG_GUARD_END
 }

@@ -48,6 +48,7 @@ struct DLevel {
     SliceMeta* slices = nullptr;
     int32_t* sell_col = nullptr;
     double* vals = nullptr;  // flat A_l
+    double *Lg = nullptr, *Mg = nullptr;  // flat P^T L P and P^T M P of this level (fast t updates; level 0: L, M)
     double* dinv = nullptr;
     float* vals32 = nullptr;
     float* dinv32 = nullptr;
@@ -100,6 +101,9 @@ struct smg_hierarchy {
     double* facegrad = nullptr;    // 9 per face, allocated by the first derivative call
     double* dt_face = nullptr;
     bool have_positions = false, have_matrix = false;
+    bool split_valid = false;             // Lg / Mg of every level match the current positions
+    double* t_fast = nullptr;             // t of the fast update (device scalar)
+    cudaGraphExec_t fast_t_exec = nullptr;  // per-level A = M + t L, level preparation, coarsest factor
     // solve state
     smg::SolveState* state = nullptr;
     smg::SolveState* state_host = nullptr;  // pinned

@@ -724,6 +724,31 @@ __global__ void combine_devt(int64_t nflat, int64_t n, int64_t dense_n, const do
     vals[e] = v;
 }
 
+// Fast parameter update (App. "Fast Data Smoothing"): with P^T L P and P^T M P
+// of every level kept, A_l(t) = P^T M P + t P^T L P is one pass per level.
+__global__ void axpy_devt(int64_t nflat, const double* __restrict__ t, const double* __restrict__ Lv,
+                          const double* __restrict__ Mv, double* __restrict__ vals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nflat) return;
+    vals[e] = Mv[e] + t[0] * Lv[e];
+}
+
+// Flat level-0 values of the lumped mass: the diagonal entries, zero elsewhere.
+__global__ void mass_flat(int64_t nflat, int64_t n, int64_t dense_n, const double* __restrict__ M,
+                          double* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nflat) return;
+    double v = 0.0;
+    if (dense_n > 0) {
+        if (e / dense_n == e % dense_n) v = M[e / dense_n];
+    } else if (e < n) {
+        v = M[e];
+    }
+    out[e] = v;
+}
+
+__global__ void set_scalar(double* __restrict__ d, double v) { d[0] = v; }
+
 // User-supplied level-0 values (natural CSR) scattered to the flat layout.
 __global__ void scatter_user(int64_t nflat, const int64_t* __restrict__ map, const double* __restrict__ user,
                              double* __restrict__ vals) {

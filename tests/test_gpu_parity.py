@@ -256,3 +256,28 @@ def test_batch_matches_individual_solves_and_oracle():
     for c in cases:
         c.h.set_options(rtol=1e-10, precision=smg.FP64)
     batch.close()
+
+
+def test_fast_t_updates_match_oracle_galerkin_chain():
+    """App. "Fast Data Smoothing": update_t forms every level from the kept
+    P^T M P and P^T L P; each level must equal the oracle's Galerkin chain of
+    A = M + t L for the new t, across repeated t changes and new positions."""
+    V, F = synth.perturbed_icosphere(4, seed=6)
+    c = Case(V, F, 1e-3, min_coarse=100)
+    Ps = [c.plan.prolongation_csr(l) for l in range(1, c.plan.num_levels)]
+    for Vk, t in ((V, 3e-3), (V, 0.1), (V, 1e-4), (synth.perturbed_icosphere(4, seed=7)[0], 0.02)):
+        if Vk is not V:
+            c.h.update_positions(to_dev(Vk), 1e-3)
+        c.h.update_t(t)
+        levels = oracle.build_levels(oracle.system_matrix(Vk, F, t), Ps)
+        for l in range(c.plan.num_levels):
+            got = c.h.level_matrix(l)
+            ref = levels[l].A.data
+            assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), (t, l)
+        b = synth.uniform_rhs(c.n, seed=9)
+        c.h.set_options(rtol=1e-10)
+        x, info = c.h.solve(to_dev(b))
+        ref = oracle.solve(levels, b, opt=oracle.Options(rtol=1e-10))
+        assert info["cycles"] == ref.cycles
+        assert rel(x.cpu().numpy(), ref.x) <= CYCLE_TOL
+    c.h.close()
