@@ -44,10 +44,12 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 
 // Entries per lane loaded ahead of the dependency wait.  With one lane per row
 // (the finest level, valence ~6) six entries cover a typical row and keep the
-// kernel at 48 registers, five resident blocks per SM.
+// kernel at 48 registers, five resident blocks per SM; with two lanes per row
+// (the first coarse level, rows of 15-25 entries) twelve per lane keep rows
+// out of the path that loads entries after the wait.
 template <typename T, int K, int R>
 struct Pre {
-    static constexpr int value = R == 1 ? 6 : ((K <= 2 || sizeof(T) == 4) ? 8 : 4);
+    static constexpr int value = R == 1 ? 6 : (R == 2 && K == 1) ? 12 : ((K <= 2 || sizeof(T) == 4) ? 8 : 4);
 };
 template <int K, int R>
 struct MinBlocks {
