@@ -136,14 +136,34 @@ __device__ __forceinline__ void tri_index(int b, int& ii, int& kk) {
     kk = b - t * (t + 1) / 2;
 }
 
-// Trailing update A_ik -= L_ij L_kj^T for j < k <= i.
-__global__ void __launch_bounds__(kQR * NB) k_chol_update(double* __restrict__ C, int64_t np, int j) {
+// Trailing update A_ik -= L_ij L_kj^T for first <= k <= i (tiles of the
+// triangle from block `first` on; first = j + 1 is the whole trailing matrix).
+__global__ void __launch_bounds__(kQR * NB) k_chol_update(double* __restrict__ C, int64_t np, int j, int first) {
     __shared__ double li[kQR][NB + 1];
     __shared__ double lk[NB][NB + 1];
     int ii, kk;
     tri_index(blockIdx.x / kQ, ii, kk);
     const int q0 = (blockIdx.x % kQ) * kQR;
-    const int i = j + 1 + ii, k = j + 1 + kk;
+    const int i = first + ii, k = first + kk;
+    const int rl = threadIdx.x / NB, c = threadIdx.x % NB;
+    li[rl][c] = C[((int64_t)i * NB + q0 + rl) * np + (int64_t)j * NB + c];
+#pragma unroll
+    for (int q = 0; q < kQ; q++) lk[rl + kQR * q][c] = C[((int64_t)k * NB + rl + kQR * q) * np + (int64_t)j * NB + c];
+    __syncthreads();
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < NB; q++) s[q & 3] += li[rl][q] * lk[c][q];
+    C[((int64_t)i * NB + q0 + rl) * np + (int64_t)k * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
+}
+
+// Look-ahead part of the trailing update: block column k = j + 1 only
+// (A_i,j+1 -= L_ij L_j+1,j^T for i >= j + 1), which is all the next diagonal
+// tile and panel need.
+__global__ void __launch_bounds__(kQR * NB) k_chol_update_col(double* __restrict__ C, int64_t np, int j) {
+    __shared__ double li[kQR][NB + 1];
+    __shared__ double lk[NB][NB + 1];
+    const int i = j + 1 + blockIdx.x / kQ, k = j + 1;
+    const int q0 = (blockIdx.x % kQ) * kQR;
     const int rl = threadIdx.x / NB, c = threadIdx.x % NB;
     li[rl][c] = C[((int64_t)i * NB + q0 + rl) * np + (int64_t)j * NB + c];
 #pragma unroll
@@ -279,21 +299,39 @@ void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s) {
     const int nb = (int)(np / NB);
     // Cholesky steps on `s`; block row j of the inverse factor needs only diagonal
     // tile j and panel j, so the inverse runs on a second stream one step behind
-    cudaStream_t s2 = h->aux;
+    cudaStream_t s2 = h->aux, s3 = h->aux2;
     k_pad_copy<<<(unsigned)((np * np + 255) / 256), 256, 0, s>>>(C.vals, C.n, C.chol, C.linv, np);
+    // look-ahead: after panel j the main stream updates only block column j + 1
+    // (what diagonal tile j + 1 and panel j + 1 need); the rest of the trailing
+    // update runs on s3, one step behind, and the main stream waits for it only
+    // before it next touches those tiles
+    bool forked3 = false;  // s3 joins the captured work only once it has some
     for (int j = 0; j < nb; j++) {
         k_chol_diag<<<1, 32 * kDiagWarps, 0, s>>>(C.chol, np, j, C.rinv, &h->state->chol_bad);
         k_tile_inv<<<kQ, 128, 0, s>>>(C.chol, np, j, C.rinv, C.dblk);
         const int T = nb - j - 1;
         if (T > 0) k_chol_panel<<<T * kQ, kQR * NB, 0, s>>>(C.chol, np, j, C.dblk);
         cudaEventRecord(h->ev_step[j], s);
-        if (T > 0) k_chol_update<<<T * (T + 1) / 2 * kQ, kQR * NB, 0, s>>>(C.chol, np, j);
+        if (T > 1) {  // block columns j + 2 .. on s3
+            forked3 = true;
+            cudaStreamWaitEvent(s3, h->ev_step[j], 0);
+            k_chol_update<<<(T - 1) * T / 2 * kQ, kQR * NB, 0, s3>>>(C.chol, np, j, j + 2);
+            cudaEventRecord(h->ev_rest[j], s3);
+        }
+        if (T > 0) {
+            if (j > 0 && nb - j > 1) cudaStreamWaitEvent(s, h->ev_rest[j - 1], 0);  // columns >= j + 1 of step j - 1
+            k_chol_update_col<<<T * kQ, kQR * NB, 0, s>>>(C.chol, np, j);
+        }
         cudaStreamWaitEvent(s2, h->ev_step[j], 0);
         k_trinv_row<<<j + 1, NB * NB, 0, s2>>>(C.linv, np, j, C.dblk);
         if (j + 1 < nb) k_trinv_update<<<(nb - j - 1) * (j + 1) * kQ, kQR * NB, 0, s2>>>(C.linv, C.chol, np, j);
     }
     cudaEventRecord(h->ev_join, s2);
     cudaStreamWaitEvent(s, h->ev_join, 0);
+    if (forked3) {
+        cudaEventRecord(h->ev_join2, s3);
+        cudaStreamWaitEvent(s, h->ev_join2, 0);
+    }
     k_transpose<<<dim3(nb, nb), NB * NB, 0, s>>>(C.linv, C.linvT, np);
 }
 

@@ -849,9 +849,13 @@ void free_all(smg_hierarchy* h) {
     if (h->state_host) cudaFreeHost(h->state_host);
     for (auto e : h->ev_step)
         if (e) cudaEventDestroy(e);
+    for (auto e : h->ev_rest)
+        if (e) cudaEventDestroy(e);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->aux2) cudaStreamDestroy(h->aux2);
     h->allocs.clear();
 }
 
@@ -861,6 +865,7 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
     h->H = (int)P.L.size() - 1;
     ck(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     ck(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking), "cudaStreamCreate");
+    ck(cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking), "cudaStreamCreate");
     h->L.resize(P.L.size());
     for (int l = 0; l <= h->H; l++) {
         const LevelPlan& lp = P.L[l];
@@ -895,7 +900,10 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
             L.rinv = dalloc<double>(h, L.np);
             h->ev_step.assign(L.np / kDenseNB, nullptr);
             for (auto& e : h->ev_step) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+            h->ev_rest.assign(L.np / kDenseNB, nullptr);
+            for (auto& e : h->ev_rest) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
             ck(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event");
+            ck(cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming), "event");
             L.y = dalloc<double>(h, L.n * kMaxRhs);
             for (double* p : {L.chol, L.linv, L.linvT}) ck(cudaMemset(p, 0, sizeof(double) * L.np * L.np), "memset");
             continue;

@@ -116,6 +116,9 @@ struct smg_hierarchy {
     cudaStream_t aux = nullptr;             // second capture stream (parallel graph branch)
     std::vector<cudaEvent_t> ev_step;       // fork points of the coarsest factorisation
     cudaEvent_t ev_join = nullptr;
+    cudaStream_t aux2 = nullptr;            // third capture stream (look-ahead trailing updates)
+    std::vector<cudaEvent_t> ev_rest;       // trailing update of step j done (block columns j + 2 ..)
+    cudaEvent_t ev_join2 = nullptr;
     cudaGraphExec_t update_exec = nullptr;
     std::map<int, cudaGraphExec_t> solve_exec;   // key precision * 16 + nrhs
     std::map<int, cudaGraphExec_t> cycle_exec;   // key precision * 16 + nrhs
