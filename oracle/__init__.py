@@ -278,6 +278,8 @@ class Options:
     post_reverse: bool = True        # post-relaxation visits the colour classes in reverse
     rtol: float = 1e-10
     max_cycles: int = 100
+    smoother: str = "gs"             # "gs" (Sec. 5) or "jacobi" (damped; App. "Ablation Study")
+    omega: float = 2.0 / 3.0         # Jacobi damping (the paper gives none; 2/3 is the textbook weight)
 
 
 def build_levels(A0, Ps):
@@ -299,10 +301,23 @@ def build_levels(A0, Ps):
     return levels
 
 
-def relax(lv, x, b, sweeps, reverse, single=False):
+def jacobi_sweep(A, x, b, omega):
+    """One damped Jacobi pass: x <- x + omega D^{-1} (b - A x), every row from the
+    old iterate (App. "Ablation Study"); x (n or n x k) is updated in place."""
+    d = A.diagonal().reshape(-1, *([1] * (x.ndim - 1)))
+    r = b - A @ x
+    x += (omega * r / d).astype(x.dtype)
+    return x
+
+
+def relax(lv, x, b, sweeps, reverse, single=False, opt=None):
     A = lv.A32 if single else lv.A
+    jacobi = opt is not None and opt.smoother == "jacobi"
     for _ in range(sweeps):
-        gs_sweep(A, x, b, lv.rev if reverse else lv.fwd)
+        if jacobi:
+            jacobi_sweep(A, x, b, np.float32(opt.omega) if single else opt.omega)
+        else:
+            gs_sweep(A, x, b, lv.rev if reverse else lv.fwd)
     return x
 
 
@@ -317,14 +332,14 @@ def vcycle(levels, h, x, b, opt, single=False):
         return chol_solve(lv.L, b)
     A = lv.A32 if single else lv.A
     P = lv.P32 if single else lv.P
-    x = relax(lv, x, b, opt.mu_pre, False, single)                    # pre-relaxation
+    x = relax(lv, x, b, opt.mu_pre, False, single, opt)               # pre-relaxation
     r = P.T @ (b - A @ x)                                             # restrict residual
     nc = levels[h + 1].A.shape[0]
     zero = np.zeros((nc,) + b.shape[1:], dtype=b.dtype)
     c = vcycle(levels, h + 1, zero, r, opt, single)                   # coarse correction
     x = x + P @ c                                                     # prolong and add
     x = np.ascontiguousarray(x)
-    x = relax(lv, x, b, opt.mu_post, opt.post_reverse, single)        # post-relaxation
+    x = relax(lv, x, b, opt.mu_post, opt.post_reverse, single, opt)   # post-relaxation
     return x
 
 

@@ -276,3 +276,51 @@ def test_dirichlet_drops_empty_coarse_columns():
     assert list(keep) == [0, 1]
     assert Ps[0].shape == (5, 2) and Ps[1].shape == (2, 2)
     assert np.allclose(Ps[1].toarray(), np.eye(2))
+
+
+# ---------------------------------------------------------------------------
+# damped Jacobi relaxation (App. "Ablation Study")
+# ---------------------------------------------------------------------------
+def test_jacobi_sweep_damps_grid_eigenmodes_by_closed_form():
+    """On the right-triangle grid the operator is the 5-point stencil with a
+    constant diagonal 4 (times the spacing factor), so a sine mode of the
+    interior is an eigenvector of D^{-1} A with eigenvalue
+    1 - (cos(pi p h) + cos(pi q h)) / 2 and one damped sweep on A e = 0 scales
+    the error by 1 - omega * lambda (the textbook damping factor)."""
+    m = 9
+    g = np.linspace(0.0, 1.0, m)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    V = np.stack([X.ravel(), Y.ravel(), np.zeros(m * m)], axis=1)
+    F = []
+    for i in range(m - 1):
+        for j in range(m - 1):
+            a, b_, c, d = i * m + j, (i + 1) * m + j, (i + 1) * m + j + 1, i * m + j + 1
+            F += [[a, b_, c], [a, c, d]]
+    F = np.array(F)
+    L = oracle.cotan_laplacian(V, F).tocsr()
+    inner = np.array([i * m + j for i in range(1, m - 1) for j in range(1, m - 1)])
+    Li = L[inner][:, inner].tocsr()
+    h = 1.0 / (m - 1)
+    omega = 2.0 / 3.0
+    for p_, q_ in ((1, 1), (2, 5), (7, 7)):
+        e = np.array([np.sin(np.pi * p_ * X.ravel()[k]) * np.sin(np.pi * q_ * Y.ravel()[k]) for k in inner])
+        lam = 1.0 - (np.cos(np.pi * p_ * h) + np.cos(np.pi * q_ * h)) / 2.0
+        x = e.copy()
+        oracle.jacobi_sweep(Li, x, np.zeros_like(e), omega)
+        assert np.abs(x - (1.0 - omega * lam) * e).max() <= 1e-12
+
+
+def test_jacobi_cycle_keeps_the_solution_fixed_and_converges(torus_pin_hierarchy):
+    V, F, Ps = torus_pin_hierarchy
+    A = oracle.system_matrix(V, F, 1e-3)
+    levels = oracle.build_levels(A, Ps)
+    b = synth.uniform_rhs(A.shape[0], nrhs=2, seed=31)
+    xs = spla.splu(A.tocsc()).solve(b)
+    opt = oracle.Options(smoother="jacobi", rtol=1e-10, max_cycles=200)
+    x1 = oracle.vcycle(levels, 0, xs.copy(), b, opt)
+    assert np.abs(x1 - xs).max() <= 1e-12 * np.abs(xs).max()   # the solution is a fixed point
+    res = oracle.solve(levels, b, opt=opt)
+    assert oracle.rel_residual(A, res.x, b) <= 1e-10
+    assert oracle.convergence_factor(res.history) < 1.0
+    gs = oracle.solve(levels, b, opt=oracle.Options(rtol=1e-10))
+    assert gs.cycles <= res.cycles   # Gauss-Seidel smooths better per sweep
