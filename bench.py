@@ -304,6 +304,27 @@ def run_ours(args, w, rank, world, local_rank):
         ms_cg, it_cg = timed_steps(args.steps, p, smg.PCG)
         pcg[name] = {"time_to_tol_ms": sum(ms_cg) / len(ms_cg), "iterations_per_solve": it_cg[0],
                      "V-cycles/s": sum(it_cg) * world / (sum(ms_cg) / 1e3)}
+    # App. "Ablation Study": relaxation method x mu (same hierarchy, binary64 solves)
+    ablation = []
+    for sm_name, sm in (("gauss-seidel", smg.GS), ("jacobi", smg.JACOBI)):
+        for mu in (1, 2, 3):
+            h.set_options(rtol=w["rtol"], max_cycles=400, precision=smg.FP64, mu_pre=mu, mu_post=mu, smoother=sm)
+            for _ in range(2):  # graph instantiation
+                step(smg.FP64)
+                torch.cuda.synchronize()
+                h.solve_result()
+            ts, cs = [], []
+            for i in range(2):
+                flush.fill_(i)
+                a0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                step(smg.FP64)
+                e0.record(stream)
+                torch.cuda.synchronize()
+                info = h.solve_result()
+                ts.append(a0.elapsed_time(e0))
+                cs.append(info["cycles"])
+            ablation.append({"smoother": sm_name, "mu": mu, "cycles": cs[0], "time_to_tol_ms": min(ts)})
     h.set_options(rtol=w["rtol"], max_cycles=200, precision=smg.FP64)
 
     # stage timings with CUDA events on this stream (L2 flushed before each)
@@ -408,6 +429,7 @@ def run_ours(args, w, rank, world, local_rank):
         "mixed": {"value": sum(cyc_mx) * world / (sum(ms_mx) / 1e3), "ms_per_step": sum(ms_mx) / len(ms_mx),
                   "refinement_steps_per_solve": cyc_mx[0]},
         "pcg": pcg,
+        "ablation": ablation,
         "roofline": {"kernel": "gs_colour<double,1> level-0 sweep (all colour launches)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": captured_traffic(), "traffic_source": "ncu dram__bytes_read.sum + "

@@ -49,6 +49,11 @@ extern "C" {
 #define SMG_MIXED 1   /* binary32 V-cycles inside binary64 iterative refinement; the
                          residual, the update and the coarsest Cholesky stay binary64 */
 
+#define SMG_SMOOTHER_GS     0  /* multicolour Gauss-Seidel (Sec. 5, App. "Multi-Color Gauss Seidel") */
+#define SMG_SMOOTHER_JACOBI 1  /* damped Jacobi x <- x + omega D^{-1} (b - A x), the alternative
+                                  App. "Ablation Study" compares; two launches per sweep instead of
+                                  one per colour class; the cluster tail is not used with it */
+
 #define SMG_SOLVER_VCYCLE 0  /* Alg. 1: repeat V-cycles while the relative residual exceeds rtol */
 #define SMG_SOLVER_PCG    1  /* conjugate gradients preconditioned by one V-cycle from a zero start
                                 (Sec. "Limitations & Future Work"); the cycle is symmetric when
@@ -69,6 +74,7 @@ typedef void *smg_stream;   /* a cudaStream_t */
  *   post_reverse 1: post-relaxation visits the colour classes in reverse order
  *                (symmetric cycle); 0: same order as pre-relaxation
  *   solver       SMG_SOLVER_VCYCLE (default) or SMG_SOLVER_PCG
+ *   smoother     SMG_SMOOTHER_GS (default) or SMG_SMOOTHER_JACOBI (jacobi_omega)
  *   autotune     1: smg_create times the smoother kernels of every level with
  *                1, 2, 4, 8 and 16 lanes per matrix row and keeps the fastest,
  *                then times whole cycles to choose the first level of the
@@ -88,6 +94,8 @@ typedef struct smg_options {
     int32_t post_reverse;
     int32_t autotune;
     int32_t solver;        /* SMG_SOLVER_VCYCLE or SMG_SOLVER_PCG */
+    int32_t smoother;      /* SMG_SMOOTHER_GS (default) or SMG_SMOOTHER_JACOBI */
+    double  jacobi_omega;  /* damping of SMG_SMOOTHER_JACOBI, in (0, 2); default 2/3 */
 } smg_options;
 
 /* Result of one solve (host struct filled by smg_solve). */

@@ -16,10 +16,11 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Plan", "Hierarchy", "Batch", "differentiable_solve", "differentiable_mass", "SmgError", "Options", "Info", "FP64", "MIXED", "VCYCLE", "PCG", "lib", "library_path"]
+__all__ = ["Plan", "Hierarchy", "Batch", "differentiable_solve", "differentiable_mass", "SmgError", "Options", "Info", "FP64", "MIXED", "VCYCLE", "PCG", "GS", "JACOBI", "lib", "library_path"]
 
 FP64, MIXED = 0, 1
 VCYCLE, PCG = 0, 1  # solver: Alg. 1 V-cycle iteration, or CG preconditioned by one V-cycle
+GS, JACOBI = 0, 1  # smoother: multicolour Gauss-Seidel, or damped Jacobi
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "non-manifold mesh", 3: "decimation failed",
           4: "not SPD", 5: "not converged", 6: "diverged", 7: "timeout", 8: "CUDA error",
@@ -31,7 +32,8 @@ class Options(ctypes.Structure):
                 ("min_coarse", ctypes.c_int64), ("max_coarse", ctypes.c_int64),
                 ("max_levels", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("post_reverse", ctypes.c_int32), ("autotune", ctypes.c_int32), ("solver", ctypes.c_int32)]
+                ("post_reverse", ctypes.c_int32), ("autotune", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("smoother", ctypes.c_int32), ("jacobi_omega", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

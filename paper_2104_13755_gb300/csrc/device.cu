@@ -105,6 +105,27 @@ void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse,
 }
 
 template <typename T, int K>
+void rec_residual(DLevel& L, const LevelView<T>& v, cudaStream_t s);
+
+// One relaxation sweep of the configured smoother: multicolour Gauss-Seidel,
+// or damped Jacobi (r = b - A x into the level's residual buffer, then
+// x += omega D^{-1} r).
+template <typename T, int K>
+void rec_relax(const smg_hierarchy* h, DLevel& L, const LevelView<T>& v, bool reverse, cudaStream_t s) {
+    if (h->opts.smoother != SMG_SMOOTHER_JACOBI) {
+        rec_sweep<T, K>(L, v, v.b, v.x, reverse, s);
+        return;
+    }
+    rec_residual<T, K>(L, v, s);
+    const T w = (T)h->opts.jacobi_omega;
+    const T* di = v.dinv;
+    const T* r = v.r;
+    ck(launch_pdl(kern::jacobi_update<T, K>, dim3(blocks_for(L.n * K)), dim3(kern::kThreads), s, (int64_t)L.n, w, di,
+                  r, v.x),
+       "jacobi launch");
+}
+
+template <typename T, int K>
 void rec_residual(DLevel& L, const LevelView<T>& v, cudaStream_t s) {
     const int R = lanes<T>(L);
     const dim3 grid(blocks_for((int64_t)L.nslices * 32 * R)), block(kern::kThreads);
@@ -147,7 +168,7 @@ size_t tail_bytes(const smg_hierarchy* h, int t, bool single, int K) {
 // First tail level for K right-hand sides: the tuned level, moved down while its
 // shared memory does not fit in one CTA.
 int tail_start(const smg_hierarchy* h, bool single, int K) {
-    if (h->tail_cluster == 0 || h->H == 0) return h->H;
+    if (h->tail_cluster == 0 || h->H == 0 || h->opts.smoother == SMG_SMOOTHER_JACOBI) return h->H;
     int t = std::min(single ? h->tail32 : h->tail64, h->H);
     while (t < h->H && tail_bytes(h, t, single, K) > kTailSmemMax) t++;
     return t;
@@ -184,7 +205,7 @@ void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
         DLevel& N = h->L[l + 1];
         LevelView<T> v = view<T>(L);
         LevelView<T> vn = view<T>(N);
-        for (int it = 0; it < h->opts.mu_pre; it++) rec_sweep<T, K>(L, v, v.b, v.x, false, s);  // pre-relaxation
+        for (int it = 0; it < h->opts.mu_pre; it++) rec_relax<T, K>(h, L, v, false, s);  // pre-relaxation
         rec_residual<T, K>(L, v, s);
         const dim3 grid(blocks_for(N.n * 4)), block(kern::kThreads);
         const T* r = v.r;
@@ -205,7 +226,7 @@ void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
         const T* xc = vn.x;
         ck(launch_pdl(kern::prolong_add<T, K>, grid, block, s, (int)L.n, (const int32_t*)L.p_idx, v.p_w, xc, v.x),
            "prolong launch");
-        for (int it = 0; it < h->opts.mu_post; it++) rec_sweep<T, K>(L, v, v.b, v.x, h->opts.post_reverse != 0, s);
+        for (int it = 0; it < h->opts.mu_post; it++) rec_relax<T, K>(h, L, v, h->opts.post_reverse != 0, s);
     }
 }
 
@@ -1070,9 +1091,13 @@ int smg_create(const smg_plan* plan, const smg_options* opts, smg_hierarchy** ou
         o.post_reverse = opts->post_reverse;
         o.autotune = opts->autotune;
         o.solver = opts->solver;
+        o.smoother = opts->smoother;
+        o.jacobi_omega = opts->jacobi_omega;
     }
     if (o.mu_pre < 0 || o.mu_post < 0 || o.max_cycles < 0 || !(o.rtol >= 0) ||
-        (o.solver != SMG_SOLVER_VCYCLE && o.solver != SMG_SOLVER_PCG))
+        (o.solver != SMG_SOLVER_VCYCLE && o.solver != SMG_SOLVER_PCG) ||
+        (o.smoother != SMG_SMOOTHER_GS && o.smoother != SMG_SMOOTHER_JACOBI) ||
+        !(o.jacobi_omega > 0.0 && o.jacobi_omega < 2.0))
         return fail("invalid solve options", SMG_ERR_INVALID_ARG);
     smg_hierarchy* h = new (std::nothrow) smg_hierarchy();
     if (!h) return SMG_ERR_NO_MEMORY;
@@ -1114,7 +1139,9 @@ int smg_set_options(smg_hierarchy* h, const smg_options* o) {
     if (!h || !o) return fail("null argument", SMG_ERR_INVALID_ARG);
     if (o->mu_pre < 0 || o->mu_post < 0 || o->max_cycles < 0 || !(o->rtol >= 0) ||
         (o->precision != SMG_FP64 && o->precision != SMG_MIXED) ||
-        (o->solver != SMG_SOLVER_VCYCLE && o->solver != SMG_SOLVER_PCG))
+        (o->solver != SMG_SOLVER_VCYCLE && o->solver != SMG_SOLVER_PCG) ||
+        (o->smoother != SMG_SMOOTHER_GS && o->smoother != SMG_SMOOTHER_JACOBI) ||
+        !(o->jacobi_omega > 0.0 && o->jacobi_omega < 2.0))
         return fail("invalid solve options", SMG_ERR_INVALID_ARG);
     h->opts.mu_pre = o->mu_pre;
     h->opts.mu_post = o->mu_post;
@@ -1123,6 +1150,8 @@ int smg_set_options(smg_hierarchy* h, const smg_options* o) {
     h->opts.precision = o->precision;
     h->opts.post_reverse = o->post_reverse;
     h->opts.solver = o->solver;
+    h->opts.smoother = o->smoother;
+    h->opts.jacobi_omega = o->jacobi_omega;
     drop_graphs(h);
     return SMG_OK;
 }

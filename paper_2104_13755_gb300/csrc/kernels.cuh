@@ -152,6 +152,19 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) gs_colour(co
         for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = (b[(int64_t)row * K + q] + acc[q]) * d;
 }
 
+// Damped Jacobi update x <- x + omega D^{-1} r after r = b - A x (App.
+// "Ablation Study": the smoother compared with Gauss-Seidel).
+template <typename T, int K>
+__global__ void jacobi_update(int64_t n, T omega, const T* __restrict__ dinv, const T* __restrict__ r,
+                              T* __restrict__ x) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * K) return;
+    const T w = omega * dinv[e / K];
+    pdl_wait();
+    pdl_trigger();
+    x[e] += w * r[e];
+}
+
 // r = b - A x over all rows of a level.
 template <typename T, int K, int R>
 __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) residual(const SliceMeta* __restrict__ slices, int nslices,

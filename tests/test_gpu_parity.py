@@ -281,3 +281,28 @@ def test_fast_t_updates_match_oracle_galerkin_chain():
         assert info["cycles"] == ref.cycles
         assert rel(x.cpu().numpy(), ref.x) <= CYCLE_TOL
     c.h.close()
+
+
+@pytest.mark.parametrize("smoother,mu,ratio", [("jacobi", 2, 0.25), ("jacobi", 1, 0.5), ("gs", 1, 0.5),
+                                               ("gs", 3, 0.25)])
+def test_ablation_settings_match_oracle(smoother, mu, ratio):
+    """App. "Ablation Study": relaxation method (multicolour Gauss-Seidel or
+    damped Jacobi), mu_pre = mu_post in {1, 2, 3}, coarsening ratio 0.25 or 0.5;
+    every cycle iterate against the oracle with the same settings."""
+    V, F = synth.torus(96, 32, seed=5)
+    sm = smg.JACOBI if smoother == "jacobi" else smg.GS
+    c = Case(V, F, 1e-3, min_coarse=100, ratio=ratio, mu_pre=mu, mu_post=mu, smoother=sm)
+    opt = oracle.Options(mu_pre=mu, mu_post=mu, smoother=smoother)
+    b = synth.uniform_rhs(c.n, nrhs=2, seed=13)
+    x_or = np.zeros_like(b)
+    x_gpu = to_dev(x_or.copy())
+    bd = to_dev(b)
+    for k in range(4):
+        x_or = oracle.vcycle(c.levels, 0, np.ascontiguousarray(x_or), b, opt)
+        c.h.vcycle(bd, x_gpu)
+        assert rel(x_gpu.cpu().numpy(), x_or) <= CYCLE_TOL, k
+    c.h.set_options(rtol=1e-10, max_cycles=300, mu_pre=mu, mu_post=mu, smoother=sm, precision=smg.MIXED)
+    x, info = c.h.solve(bd)
+    assert info["return"] == 0
+    assert oracle.rel_residual(c.A, x.cpu().numpy(), b) <= 1e-10
+    c.h.close()
