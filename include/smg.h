@@ -75,6 +75,7 @@ typedef void *smg_stream;   /* a cudaStream_t */
  *                (symmetric cycle); 0: same order as pre-relaxation
  *   solver       SMG_SOLVER_VCYCLE (default) or SMG_SOLVER_PCG
  *   smoother     SMG_SMOOTHER_GS (default) or SMG_SMOOTHER_JACOBI (jacobi_omega)
+ *   pattern_rings  plan option: 1 or 2 (see the field)
  *   autotune     1: smg_create times the smoother kernels of every level with
  *                1, 2, 4, 8 and 16 lanes per matrix row and keeps the fastest,
  *                then times whole cycles to choose the first level of the
@@ -96,6 +97,9 @@ typedef struct smg_options {
     int32_t solver;        /* SMG_SOLVER_VCYCLE or SMG_SOLVER_PCG */
     int32_t smoother;      /* SMG_SMOOTHER_GS (default) or SMG_SMOOTHER_JACOBI */
     double  jacobi_omega;  /* damping of SMG_SMOOTHER_JACOBI, in (0, 2); default 2/3 */
+    int32_t pattern_rings; /* level-0 sparsity: 1 (default) the 1-ring of the cotangent
+                              Laplacian; 2 the 2-ring of the Bilaplacian and squared-Hessian
+                              energies (Sec. 6 "Applications"), filled by smg_update_matrix */
 } smg_options;
 
 /* Result of one solve (host struct filled by smg_solve). */

@@ -74,6 +74,27 @@ def mesh_pattern(n, F):
     return S
 
 
+def mesh_pattern2(n, F):
+    """Structural 2-ring pattern (Sec. 6: Bilaplacian and squared-Hessian
+    energies couple vertices joined by at most two edges): the pattern of S S
+    with S the 1-ring pattern."""
+    S = mesh_pattern(n, F)
+    S2 = (S @ S).tocsr()
+    S2.data[:] = 1.0
+    S2.sort_indices()
+    return S2
+
+
+def bilaplacian_system(V, F, t):
+    """A = M + t L M^{-1} L (data smoothing with the Bilaplacian energy, Sec. 6
+    and App. "Fast Data Smoothing" with Q = L M^{-1} L), on the 2-ring pattern."""
+    n = np.asarray(V).shape[0]
+    L = cotan_laplacian(V, F)
+    m = lumped_mass(V, F)
+    A = sp.diags(m) + t * (L @ sp.diags(1.0 / m) @ L)
+    return on_pattern(mesh_pattern2(n, F), A.tocsr())
+
+
 def on_pattern(S, C):
     """Values of C placed on the structural pattern S (pattern(C) must be a subset
     of pattern(S)); entries of S absent from C are explicit zeros."""

@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("post_reverse", ctypes.c_int32), ("autotune", ctypes.c_int32), ("solver", ctypes.c_int32),
-                ("smoother", ctypes.c_int32), ("jacobi_omega", ctypes.c_double)]
+                ("smoother", ctypes.c_int32), ("jacobi_omega", ctypes.c_double),
+                ("pattern_rings", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

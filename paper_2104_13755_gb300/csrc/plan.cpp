@@ -79,7 +79,8 @@ int build_plan(const double* V, int64_t n, const int32_t* F, int64_t m, const ui
                const smg_options& o, Plan& p, std::string& err) {
     int st = validate_mesh(V, n, F, m, err);
     if (st) return st;
-    if (!(o.ratio > 0.0 && o.ratio < 1.0) || o.mu_pre < 0 || o.mu_post < 0) {
+    if (!(o.ratio > 0.0 && o.ratio < 1.0) || o.mu_pre < 0 || o.mu_post < 0 ||
+        (o.pattern_rings != 1 && o.pattern_rings != 2)) {
         err = "invalid options";
         return SMG_ERR_INVALID_ARG;
     }
@@ -250,14 +251,39 @@ int finalize_plan(Plan& p, std::string& err) {
     {
         LevelPlan& lv = p.L[0];
         std::vector<std::vector<int32_t>> adj(lv.n);
-        for (int64_t f = 0; f < m0.m(); f++)
-            for (int c = 0; c < 3; c++) {
-                int32_t a = unk_of[m0.F[3 * f + c]], b = unk_of[m0.F[3 * f + (c + 1) % 3]];
-                if (a >= 0 && b >= 0) {
-                    adj[a].push_back(b);
-                    adj[b].push_back(a);
+        if (p.opts.pattern_rings == 2) {
+            // 2-ring (Sec. 6: Bilaplacian, squared Hessian): unknowns joined by a path of
+            // at most two mesh edges, through any vertex (known ones included, as in
+            // L M^{-1} L)
+            std::vector<std::vector<int32_t>> nb(n0);
+            for (int64_t f = 0; f < m0.m(); f++)
+                for (int c = 0; c < 3; c++) {
+                    const int32_t a = m0.F[3 * f + c], b = m0.F[3 * f + (c + 1) % 3];
+                    nb[a].push_back(b);
+                    nb[b].push_back(a);
+                }
+            for (auto& v : nb) {
+                std::sort(v.begin(), v.end());
+                v.erase(std::unique(v.begin(), v.end()), v.end());
+            }
+            for (int64_t r = 0; r < lv.n; r++) {
+                const int32_t v = p.unknowns[r];
+                for (int32_t w : nb[v]) {
+                    if (unk_of[w] >= 0) adj[r].push_back(unk_of[w]);
+                    for (int32_t z : nb[w])
+                        if (unk_of[z] >= 0) adj[r].push_back(unk_of[z]);
                 }
             }
+        } else {
+            for (int64_t f = 0; f < m0.m(); f++)
+                for (int c = 0; c < 3; c++) {
+                    int32_t a = unk_of[m0.F[3 * f + c]], b = unk_of[m0.F[3 * f + (c + 1) % 3]];
+                    if (a >= 0 && b >= 0) {
+                        adj[a].push_back(b);
+                        adj[b].push_back(a);
+                    }
+                }
+        }
         lv.rowptr.assign(lv.n + 1, 0);
         lv.col.clear();
         for (int64_t r = 0; r < lv.n; r++) {

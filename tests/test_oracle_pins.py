@@ -324,3 +324,36 @@ def test_jacobi_cycle_keeps_the_solution_fixed_and_converges(torus_pin_hierarchy
     assert oracle.convergence_factor(res.history) < 1.0
     gs = oracle.solve(levels, b, opt=oracle.Options(rtol=1e-10))
     assert gs.cycles <= res.cycles   # Gauss-Seidel smooths better per sweep
+
+
+# ---------------------------------------------------------------------------
+# 2-ring systems (Sec. 6: Bilaplacian)
+# ---------------------------------------------------------------------------
+def test_two_ring_pattern_is_graph_distance_two():
+    V, F = synth.torus(12, 6, seed=2)
+    n = V.shape[0]
+    S2 = oracle.mesh_pattern2(n, F)
+    nb = [set() for _ in range(n)]
+    for f in F:
+        for a in range(3):
+            nb[f[a]].add(f[(a + 1) % 3])
+            nb[f[(a + 1) % 3]].add(f[a])
+    for i in range(n):
+        ring2 = {i} | nb[i] | set().union(*(nb[j] for j in nb[i]))
+        assert set(S2.indices[S2.indptr[i]:S2.indptr[i + 1]]) == ring2
+
+
+def test_bilaplacian_system_identities():
+    """M + t L M^{-1} L: symmetric, A 1 = M 1 (L 1 = 0), x^T A x = x^T M x +
+    t |M^{-1/2} L x|^2 (its energy), positive definite."""
+    V, F = synth.perturbed_icosphere(2, seed=4)
+    t = 0.03
+    A = oracle.bilaplacian_system(V, F, t)
+    assert abs(A - A.T).max() <= 1e-15 * abs(A).max()
+    m = oracle.lumped_mass(V, F)
+    assert np.abs(A @ np.ones(V.shape[0]) - m).max() <= 1e-13 * m.max()
+    x = np.random.default_rng(1).standard_normal(V.shape[0])
+    L = oracle.cotan_laplacian(V, F)
+    e = x @ (m * x) + t * np.sum((L @ x) ** 2 / m)
+    assert abs(x @ (A @ x) - e) <= 1e-12 * e
+    assert np.linalg.eigvalsh(A.toarray()).min() > 0

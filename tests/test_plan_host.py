@@ -143,3 +143,28 @@ def test_plan_save_load_roundtrip(tmp_path, disk_plan):
     with pytest.raises(smg.SmgError) as e:
         smg.Plan.load(path)
     assert e.value.status == 11
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_two_ring_plan_patterns_and_colouring_match_oracle(dirichlet):
+    """pattern_rings = 2 (Sec. 6: Bilaplacian-type systems): the level-0 pattern
+    is the oracle's 2-ring pattern restricted to the unknowns, every coarse
+    pattern its Galerkin pattern, and every colouring the oracle's Alg. 3."""
+    if dirichlet:
+        V, F, known = synth.disk(24, seed=3)
+    else:
+        V, F = synth.torus(40, 16, seed=1)
+        known = np.zeros(V.shape[0], dtype=bool)
+    plan = smg.Plan(V, F, dirichlet=known if dirichlet else None, pattern_rings=2, min_coarse=60)
+    A = oracle.bilaplacian_system(V, F, 1e-3)
+    Ps = [plan.prolongation_csr(l) for l in range(1, plan.num_levels)]
+    A, Ps, u, _ = oracle.dirichlet_reduce(A, Ps, known)
+    S = A
+    for l in range(plan.num_levels):
+        rp, ci = plan.pattern(l)
+        Sp = S.tocsr()
+        Sp.sort_indices()
+        assert np.array_equal(rp, Sp.indptr) and np.array_equal(ci, Sp.indices), l
+        if l < plan.num_levels - 1:
+            assert np.array_equal(plan.colouring(l), oracle.greedy_colouring(Sp))
+            S = oracle.galerkin_pattern(Sp, Ps[l])
