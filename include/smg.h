@@ -75,7 +75,7 @@ typedef void *smg_stream;   /* a cudaStream_t */
  *                (symmetric cycle); 0: same order as pre-relaxation
  *   solver       SMG_SOLVER_VCYCLE (default) or SMG_SOLVER_PCG
  *   smoother     SMG_SMOOTHER_GS (default) or SMG_SMOOTHER_JACOBI (jacobi_omega)
- *   pattern_rings  plan option: 1 or 2 (see the field)
+ *   pattern_rings, block_size  plan options (see the fields)
  *   autotune     1: smg_create times the smoother kernels of every level with
  *                1, 2, 4, 8 and 16 lanes per matrix row and keeps the fastest,
  *                then times whole cycles to choose the first level of the
@@ -100,6 +100,11 @@ typedef struct smg_options {
     int32_t pattern_rings; /* level-0 sparsity: 1 (default) the 1-ring of the cotangent
                               Laplacian; 2 the 2-ring of the Bilaplacian and squared-Hessian
                               energies (Sec. 6 "Applications"), filled by smg_update_matrix */
+    int32_t block_size;    /* unknowns per vertex: 1 (default) or 3 (3|V| systems such as the
+                              shell Hessians of Sec. 6): every level has 3 unknowns per vertex
+                              (x, y, z adjacent), prolongation P (x) I_3, patterns of 3 x 3
+                              blocks; smg_update_positions then assembles (M + t L) (x) I_3 and
+                              smg_update_matrix takes any SPD matrix on that pattern */
 } smg_options;
 
 /* Result of one solve (host struct filled by smg_solve). */

@@ -95,6 +95,20 @@ def bilaplacian_system(V, F, t):
     return on_pattern(mesh_pattern2(n, F), A.tocsr())
 
 
+def expand_blocks(X, bs):
+    """bs unknowns per vertex (3|V| systems of Sec. 6, components adjacent):
+    X (x) I_bs for operators and prolongations alike."""
+    return sp.kron(X, sp.identity(bs), format="csr")
+
+
+def block_pattern(S, bs):
+    """Pattern of bs x bs blocks over the vertex pattern S."""
+    B = sp.kron(S, np.ones((bs, bs)), format="csr")
+    B.data[:] = 1.0
+    B.sort_indices()
+    return B
+
+
 def on_pattern(S, C):
     """Values of C placed on the structural pattern S (pattern(C) must be a subset
     of pattern(S)); entries of S absent from C are explicit zeros."""

@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("post_reverse", ctypes.c_int32), ("autotune", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("smoother", ctypes.c_int32), ("jacobi_omega", ctypes.c_double),
-                ("pattern_rings", ctypes.c_int32)]
+                ("pattern_rings", ctypes.c_int32), ("block_size", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

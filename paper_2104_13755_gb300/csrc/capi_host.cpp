@@ -15,7 +15,7 @@ using namespace smg;
 namespace {
 // ---------------------------------------------------------------- save / load
 const char kMagic[8] = {'S', 'M', 'G', 'P', 'L', 'A', 'N', '1'};
-const int32_t kVersion = 5;  // 3: smg_options gained `solver`; 4: `smoother`, `jacobi_omega`; 5: `pattern_rings`
+const int32_t kVersion = 6;  // 3: smg_options gained `solver`; 4: `smoother`, `jacobi_omega`; 5: `pattern_rings`; 6: `block_size`
 
 template <class T>
 bool wvec(FILE* f, const std::vector<T>& v) {
@@ -51,6 +51,7 @@ void smg_default_options(smg_options* o) {
     o->smoother = SMG_SMOOTHER_GS;
     o->jacobi_omega = 2.0 / 3.0;
     o->pattern_rings = 1;
+    o->block_size = 1;
 }
 
 const char* smg_status_string(int s) {

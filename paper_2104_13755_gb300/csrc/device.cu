@@ -1512,6 +1512,7 @@ int smg_batch_solve(smg_batch* B, const double* b, double* x, int nrhs, smg_info
 
 int smg_lumped_mass(smg_hierarchy* h, const double* V, double* m, smg_stream stream) {
     if (!h || !V || !m) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (h->opts.block_size != 1) return fail("position derivatives need one unknown per vertex", SMG_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     SMG_GUARD_BEGIN
     kern::face_geom<<<blocks_for(h->nf), kern::kThreads, 0, s>>>(h->nf, h->F, V, h->facegeom);
@@ -1531,6 +1532,7 @@ static void ensure_face_scratch(smg_hierarchy* h) {
 
 int smg_mass_grad(smg_hierarchy* h, const double* V, const double* w, double* gradV, smg_stream stream) {
     if (!h || !V || !w || !gradV) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (h->opts.block_size != 1) return fail("position derivatives need one unknown per vertex", SMG_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     SMG_GUARD_BEGIN
     ensure_face_scratch(h);
@@ -1546,6 +1548,7 @@ int smg_mass_grad(smg_hierarchy* h, const double* V, const double* w, double* gr
 int smg_operator_grad(smg_hierarchy* h, const double* V, double t, const double* lam, const double* x, int nrhs,
                       double* gradV, double* dt, smg_stream stream) {
     if (!h || !V || !lam || !x || !gradV) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (h->opts.block_size != 1) return fail("position derivatives need one unknown per vertex", SMG_ERR_INVALID_ARG);
     if (nrhs < 1 || nrhs > kMaxRhs) return fail("nrhs must be 1..4", SMG_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     SMG_GUARD_BEGIN

@@ -80,7 +80,7 @@ int build_plan(const double* V, int64_t n, const int32_t* F, int64_t m, const ui
     int st = validate_mesh(V, n, F, m, err);
     if (st) return st;
     if (!(o.ratio > 0.0 && o.ratio < 1.0) || o.mu_pre < 0 || o.mu_post < 0 ||
-        (o.pattern_rings != 1 && o.pattern_rings != 2)) {
+        (o.pattern_rings != 1 && o.pattern_rings != 2) || (o.block_size != 1 && o.block_size != 3)) {
         err = "invalid options";
         return SMG_ERR_INVALID_ARG;
     }
@@ -247,10 +247,33 @@ int finalize_plan(Plan& p, std::string& err) {
     }
 
     tm.mark("dirichlet + reduced P");
+    // ---- unknowns per vertex: every vertex quantity becomes bs adjacent unknowns,
+    // the prolongation P (x) I_bs (the weights act on each component alone)
+    const int bs = p.opts.block_size;
+    const int64_t nvu = p.L[0].n;  // vertex unknowns at level 0
+    if (bs > 1) {
+        for (int l = 0; l <= H; l++) {
+            LevelPlan& lv = p.L[l];
+            if (l < H) {
+                std::vector<int32_t> idx(3 * bs * lv.n, -1);
+                std::vector<double> w(3 * bs * lv.n, 0.0);
+                for (int64_t r = 0; r < lv.n; r++)
+                    for (int d = 0; d < bs; d++)
+                        for (int a = 0; a < 3; a++) {
+                            const int32_t c = lv.pn_idx[3 * r + a];
+                            idx[3 * (bs * r + d) + a] = c < 0 ? -1 : bs * c + d;
+                            w[3 * (bs * r + d) + a] = lv.pn_w[3 * r + a];
+                        }
+                lv.pn_idx.swap(idx);
+                lv.pn_w.swap(w);
+            }
+            lv.n *= bs;
+        }
+    }
     // ---- symbolic patterns
     {
         LevelPlan& lv = p.L[0];
-        std::vector<std::vector<int32_t>> adj(lv.n);
+        std::vector<std::vector<int32_t>> adj(nvu);
         if (p.opts.pattern_rings == 2) {
             // 2-ring (Sec. 6: Bilaplacian, squared Hessian): unknowns joined by a path of
             // at most two mesh edges, through any vertex (known ones included, as in
@@ -266,7 +289,7 @@ int finalize_plan(Plan& p, std::string& err) {
                 std::sort(v.begin(), v.end());
                 v.erase(std::unique(v.begin(), v.end()), v.end());
             }
-            for (int64_t r = 0; r < lv.n; r++) {
+            for (int64_t r = 0; r < nvu; r++) {
                 const int32_t v = p.unknowns[r];
                 for (int32_t w : nb[v]) {
                     if (unk_of[w] >= 0) adj[r].push_back(unk_of[w]);
@@ -286,13 +309,16 @@ int finalize_plan(Plan& p, std::string& err) {
         }
         lv.rowptr.assign(lv.n + 1, 0);
         lv.col.clear();
-        for (int64_t r = 0; r < lv.n; r++) {
+        for (int64_t r = 0; r < nvu; r++) {
             auto& a = adj[r];
             a.push_back((int32_t)r);
             std::sort(a.begin(), a.end());
             a.erase(std::unique(a.begin(), a.end()), a.end());
-            lv.col.insert(lv.col.end(), a.begin(), a.end());
-            lv.rowptr[r + 1] = (int64_t)lv.col.size();
+        }
+        for (int64_t row = 0; row < lv.n; row++) {  // unknown row = bs * vertex + component
+            for (int32_t j : adj[row / bs])
+                for (int e = 0; e < bs; e++) lv.col.push_back(bs * j + e);
+            lv.rowptr[row + 1] = (int64_t)lv.col.size();
         }
     }
     for (int l = 0; l < H; l++)
@@ -528,7 +554,11 @@ int finalize_plan(Plan& p, std::string& err) {
     A.nf = m0.m();
     A.F = m0.F;
     A.row_vertex.resize(l0.n);
-    for (int64_t pr = 0; pr < l0.n; pr++) A.row_vertex[pr] = p.unknowns[l0.perm[pr]];
+    std::vector<int8_t> row_comp(l0.n);  // component of the row's unknown (0 when bs = 1)
+    for (int64_t pr = 0; pr < l0.n; pr++) {
+        A.row_vertex[pr] = p.unknowns[l0.perm[pr] / bs];
+        row_comp[pr] = (int8_t)(l0.perm[pr] % bs);
+    }
     {
         std::vector<int32_t> cnt(n0 + 1, 0);
         for (int64_t f = 0; f < A.nf; f++)
@@ -571,14 +601,17 @@ int finalize_plan(Plan& p, std::string& err) {
         if (l0.coarsest) {
             for (int64_t I = 0; I < l0.n; I++)
                 for (int64_t J = 0; J < l0.n; J++)
-                    if (I != J) opp_of(A.row_vertex[I], A.row_vertex[J], A.opp0[I * l0.n + J], A.opp1[I * l0.n + J]);
+                    if (I != J && row_comp[I] == row_comp[J] && A.row_vertex[I] != A.row_vertex[J])
+                        opp_of(A.row_vertex[I], A.row_vertex[J], A.opp0[I * l0.n + J], A.opp1[I * l0.n + J]);
         } else {
             for (const SliceMeta& s : l0.slices)
                 for (int rl = 0; rl < s.nrows; rl++)
                     for (int k = 0; k < s.width; k++) {
                         int64_t slot = slot_at(s, rl, k);
                         int32_t pc = l0.sell_col[slot];
-                        if (pc == s.row0 + rl) continue;
+                        if (pc == s.row0 + rl || row_comp[pc] != row_comp[s.row0 + rl] ||
+                            A.row_vertex[pc] == A.row_vertex[s.row0 + rl])
+                            continue;  // other components of a vertex, or of a neighbour: (x) I_bs
                         opp_of(A.row_vertex[s.row0 + rl], A.row_vertex[pc], A.opp0[l0.sbase + slot],
                                A.opp1[l0.sbase + slot]);
                     }

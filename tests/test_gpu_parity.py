@@ -6,6 +6,7 @@ iterate to 1e-12 relative (||x_gpu - x_oracle|| / ||x_oracle||).  The mixed form
 is held to 1e-9 relative error against a direct solve."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 import oracle
@@ -343,4 +344,54 @@ def test_bilaplacian_two_ring_system_matches_oracle(dirichlet):
         x, info = h.solve(bd)
         assert info["return"] == 0, kw
         assert rel(x.cpu().numpy(), xs) <= 1e-8, kw
+    h.close()
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_block3_systems_match_oracle(dirichlet):
+    """block_size = 3 (3|V| systems, Sec. 6): update_positions assembles
+    (M + t L) (x) I_3; a system with cross-component coupling,
+    (M + t L) (x) I_3 + s L (x) J (J the symmetric 3 x 3 tridiagonal ones, s < t /
+    sqrt 2 so the sum stays positive definite), goes through update_matrix.
+    Galerkin levels, every cycle and the solves against the oracle."""
+    if dirichlet:
+        V, F, known = synth.disk(32, seed=9)
+    else:
+        V, F = synth.torus(48, 20, seed=7)
+        known = np.zeros(V.shape[0], dtype=bool)
+    t = 1e-3
+    plan = smg.Plan(V, F, dirichlet=known if dirichlet else None, block_size=3, min_coarse=100)
+    h = smg.Hierarchy(plan)
+    n = V.shape[0]
+    S3 = oracle.block_pattern(oracle.mesh_pattern(n, F), 3)
+    Ps = [oracle.expand_blocks(plan.prolongation_csr(l), 3) for l in range(1, plan.num_levels)]
+    L = oracle.cotan_laplacian(V, F)
+    J = sp.csr_matrix(np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 1.0], [0.0, 1.0, 0.0]]))
+    systems = [("assembled", oracle.expand_blocks(oracle.system_matrix(V, F, t), 3)),
+               ("coupled", oracle.expand_blocks(oracle.system_matrix(V, F, t), 3) + 0.3 * t * sp.kron(L, J))]
+    for name, A in systems:
+        A = oracle.on_pattern(S3, A.tocsr())
+        Ar, Pr, _, _ = oracle.dirichlet_reduce(A, Ps, np.repeat(known, 3))
+        levels = oracle.build_levels(Ar, Pr)
+        if name == "assembled":
+            h.update_positions(to_dev(V), t)
+        else:
+            h.update_matrix(to_dev(Ar.data))
+        for l in range(plan.num_levels):
+            ref = levels[l].A.data
+            assert np.abs(h.level_matrix(l) - ref).max() <= 1e-13 * np.abs(ref).max(), (name, l)
+        b = synth.uniform_rhs(Ar.shape[0], nrhs=1, seed=19)
+        bd = to_dev(b)
+        x_or = np.zeros_like(b)
+        x_gpu = to_dev(x_or.copy())
+        for k in range(3):
+            x_or = oracle.vcycle(levels, 0, np.ascontiguousarray(x_or), b, oracle.Options())
+            h.vcycle(bd, x_gpu)
+            assert rel(x_gpu.cpu().numpy(), x_or) <= CYCLE_TOL, (name, k)
+        xs = spla.splu(Ar.tocsc()).solve(b)
+        for kw in (dict(), dict(precision=smg.MIXED), dict(solver=smg.PCG)):
+            h.set_options(rtol=1e-10, max_cycles=300, **kw)
+            x, info = h.solve(bd)
+            assert info["return"] == 0, (name, kw)
+            assert rel(x.cpu().numpy(), xs) <= 1e-8, (name, kw)
     h.close()

@@ -357,3 +357,24 @@ def test_bilaplacian_system_identities():
     e = x @ (m * x) + t * np.sum((L @ x) ** 2 / m)
     assert abs(x @ (A @ x) - e) <= 1e-12 * e
     assert np.linalg.eigvalsh(A.toarray()).min() > 0
+
+
+def test_block_expansion_identities():
+    """X (x) I_3: (A (x) I)(u (x) e_k) = (A u) (x) e_k, and a Galerkin product of
+    expanded operators is the expansion of the vertex Galerkin product."""
+    V, F = synth.perturbed_icosphere(2, seed=2)
+    A = oracle.system_matrix(V, F, 1e-2)
+    n = A.shape[0]
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(n)
+    A3 = oracle.expand_blocks(A, 3)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = 1.0
+        assert np.abs(A3 @ np.kron(u, e) - np.kron(A @ u, e)).max() <= 1e-14 * np.abs(A @ u).max()
+    P = sp.random(n, 20, density=0.1, random_state=4, format="csr")
+    lhs = oracle.expand_blocks(P, 3).T @ A3 @ oracle.expand_blocks(P, 3)
+    rhs = oracle.expand_blocks((P.T @ A @ P).tocsr(), 3)
+    assert abs(lhs - rhs).max() <= 1e-13 * abs(rhs).max()
+    S3 = oracle.block_pattern(oracle.mesh_pattern(n, F), 3)
+    assert S3.nnz == 9 * oracle.mesh_pattern(n, F).nnz

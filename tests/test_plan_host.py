@@ -168,3 +168,30 @@ def test_two_ring_plan_patterns_and_colouring_match_oracle(dirichlet):
         if l < plan.num_levels - 1:
             assert np.array_equal(plan.colouring(l), oracle.greedy_colouring(Sp))
             S = oracle.galerkin_pattern(Sp, Ps[l])
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_block3_plan_patterns_and_colouring_match_oracle(dirichlet):
+    """block_size = 3 (3|V| systems, Sec. 6): level 0 is the vertex pattern in
+    3 x 3 blocks over the unknowns, P is P (x) I_3, and every coarse pattern and
+    colouring follows from them as for scalar systems."""
+    if dirichlet:
+        V, F, known = synth.disk(20, seed=2)
+    else:
+        V, F = synth.perturbed_icosphere(3, seed=1)
+        known = np.zeros(V.shape[0], dtype=bool)
+    plan = smg.Plan(V, F, dirichlet=known if dirichlet else None, block_size=3, min_coarse=60)
+    A = oracle.expand_blocks(oracle.system_matrix(V, F, 1e-3), 3)
+    A = oracle.on_pattern(oracle.block_pattern(oracle.mesh_pattern(V.shape[0], F), 3), A)
+    Ps = [oracle.expand_blocks(plan.prolongation_csr(l), 3) for l in range(1, plan.num_levels)]
+    A, Ps, u, _ = oracle.dirichlet_reduce(A, Ps, np.repeat(known, 3))
+    assert plan.level_info(0)[0] == u.size
+    S = A
+    for l in range(plan.num_levels):
+        rp, ci = plan.pattern(l)
+        Sp = S.tocsr()
+        Sp.sort_indices()
+        assert np.array_equal(rp, Sp.indptr) and np.array_equal(ci, Sp.indices), l
+        if l < plan.num_levels - 1:
+            assert np.array_equal(plan.colouring(l), oracle.greedy_colouring(Sp))
+            S = oracle.galerkin_pattern(Sp, Ps[l])
