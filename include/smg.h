@@ -307,6 +307,13 @@ int  smg_level_config(const smg_hierarchy *h, int level, int32_t out[4]);
  * cluster (0 when the device offers no cluster launch). */
 int  smg_cycle_config(const smg_hierarchy *h, int32_t out[4]);
 
+/* Kernel launches of the library's calls, counted from the captured graphs
+ * (a measurement aid; the paper has no counterpart), for the current options
+ * and nrhs right-hand sides: out[0] per smg_update_positions, out[1] per
+ * smg_solve outside its cycle loop, out[2] per loop iteration (one cycle, or
+ * one CG iteration).  Builds the solve graph if it does not exist yet. */
+int  smg_launch_counts(smg_hierarchy *h, int nrhs, int32_t out[3]);
+
 /*
  * Residual norms of a system the caller holds, with no allocation at all.
  * (The paper has no counterpart: this is a service for callers that cannot

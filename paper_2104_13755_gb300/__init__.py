@@ -93,6 +93,7 @@ def _load():
         "smg_cycle_config": (I32, [P, P]),
         "smg_device_bytes": (I64, [P]),
         "smg_residual_norms_noalloc": (I32, [I64, P, P, P, P, P, I32, P, P]),
+        "smg_launch_counts": (I32, [P, I32, P]),
         "smg_operator_grad": (I32, [P, P, D, P, P, I32, P, P, P]),
         "smg_lumped_mass": (I32, [P, P, P, P]),
         "smg_mass_grad": (I32, [P, P, P, P, P]),
@@ -342,6 +343,12 @@ class Hierarchy:
         nrhs = 1 if x.dim() == 1 else x.shape[1]
         _check(lib.smg_apply_mass(self._h, _dev_ptr(x), _dev_ptr(y), nrhs, _stream_ptr(stream)), "smg_apply_mass")
         return y
+
+    def launch_counts(self, nrhs=1):
+        """(kernels per update_positions, per solve outside the loop, per loop iteration)."""
+        out = (ctypes.c_int32 * 3)()
+        _check(lib.smg_launch_counts(self._h, int(nrhs), out), "smg_launch_counts")
+        return tuple(out)
 
     def operator_grad(self, V, t, lam, x, stream=None):
         """(-d/dV lam^T A(V,t) x  as n x 3,  -lam^T L x  as a 1-element tensor)."""

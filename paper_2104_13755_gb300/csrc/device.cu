@@ -335,6 +335,20 @@ void rec_copy(smg_hierarchy* h, const double* src, double* dst, cudaStream_t s) 
     ck(launch_pdl(kern::cg_copy, dim3(blocks_for(m)), dim3(kern::kThreads), s, m, src, dst), "copy");
 }
 
+// Kernel nodes of a graph (memset and conditional nodes not counted).
+int count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+    int k = 0;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) k++;
+    }
+    return k;
+}
+
 // Append to graph g an independent branch solving one system: optional
 // prologue, ||b|| and the first stopping test, a WHILE node running one cycle
 // + residual norm + stopping test per iteration, optional epilogue after the
@@ -383,6 +397,7 @@ void add_solve_branch(smg_hierarchy* h, cudaGraph_t g, cudaStream_t s, bool mixe
     rec_final<K>(h, hnd, false, true, s);
     ck(cudaGetLastError(), "body launches");
     ck(cudaStreamEndCapture(s, &body), "end capture body");
+    h->last_body_kernels = count_kernel_nodes(body);
     if (epilogue || pcg) {
         ck(cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal), "capture epilogue");
         if (pcg) rec_copy<K>(h, h->cg_x, h->L[0].x, s);
@@ -398,6 +413,8 @@ cudaGraphExec_t build_solve_graph(smg_hierarchy* h, bool mixed) {
     cudaGraph_t g = nullptr;
     ck(cudaGraphCreate(&g, 0), "cudaGraphCreate");
     add_solve_branch<K>(h, g, h->cap, mixed, nullptr, nullptr);
+    const int key = (h->opts.solver == SMG_SOLVER_PCG ? 32 : 0) + (mixed ? 16 : 0) + K;
+    h->solve_kernels[key] = {count_kernel_nodes(g), h->last_body_kernels};
     cudaGraphExec_t exec = nullptr;
     ck(cudaGraphInstantiate(&exec, g, 0), "instantiate solve graph");
     cudaGraphDestroy(g);
@@ -851,6 +868,7 @@ void build_update_graph(smg_hierarchy* h) {
     rec_update(h, s);
     ck(cudaGetLastError(), "update launches");
     ck(cudaStreamEndCapture(s, &g), "end capture update");
+    h->update_kernels = count_kernel_nodes(g);
     ck(cudaGraphInstantiate(&h->update_exec, g, 0), "instantiate update graph");
     cudaGraphDestroy(g);
 }
@@ -1380,6 +1398,23 @@ int smg_level_config(const smg_hierarchy* h, int level, int32_t out[4]) {
     out[2] = L.ncolours;
     out[3] = L.nslices;
     return SMG_OK;
+}
+
+int smg_launch_counts(smg_hierarchy* h, int nrhs, int32_t out[3]) {
+    if (!h || !out) return fail("null argument", SMG_ERR_INVALID_ARG);
+    if (nrhs < 1 || nrhs > kMaxRhs) return fail("nrhs must be 1..4", SMG_ERR_INVALID_ARG);
+    SMG_GUARD_BEGIN
+    const bool mixed = h->opts.precision == SMG_MIXED;
+    solve_graph(h, nrhs, mixed);  // builds (and counts) it if needed
+    const int key = (h->opts.solver == SMG_SOLVER_PCG ? 32 : 0) + (mixed ? 16 : 0) + nrhs;
+    const auto it = h->solve_kernels.find(key);
+    // smg_update_positions launches four assembly kernels before its graph;
+    // smg_solve_async two gathers before and one scatter after its graph
+    out[0] = 4 + h->update_kernels;
+    out[1] = it == h->solve_kernels.end() ? -1 : 3 + it->second.first;
+    out[2] = it == h->solve_kernels.end() ? -1 : it->second.second;
+    return SMG_OK;
+    SMG_GUARD_END
 }
 
 int smg_cycle_config(const smg_hierarchy* h, int32_t out[4]) {

@@ -121,6 +121,9 @@ struct smg_hierarchy {
     cudaEvent_t ev_join2 = nullptr;
     cudaGraphExec_t update_exec = nullptr;
     std::map<int, cudaGraphExec_t> solve_exec;   // key precision * 16 + nrhs
+    std::map<int, std::pair<int, int>> solve_kernels;  // same key: kernel nodes outside / inside the loop
+    int update_kernels = 0;                       // kernel nodes of the update graph
+    int last_body_kernels = 0;                    // kernel nodes of the last captured solve-loop body
     std::map<int, cudaGraphExec_t> cycle_exec;   // key precision * 16 + nrhs
     std::vector<void*> allocs;
     int64_t bytes = 0;
