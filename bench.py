@@ -190,6 +190,20 @@ def oracle_cycle_rate(V, F, b, w, plan, cycles_per_solve, sample_cycles):
 
 
 # ---------------------------------------------------------------------------
+def aggregate_over_ranks(seconds, cycles, world, device=None):
+    """Replicas (one independent solve per rank, no collective in the data path):
+    the job's time is the slowest rank's, its cycles the sum over the ranks."""
+    if world == 1:
+        return seconds, cycles
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    c = torch.tensor([float(cycles)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(c.item()))
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import paper_2104_13755_gb300 as smg
@@ -265,13 +279,7 @@ def run_ours(args, w, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    total_s = sum(ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
-    cycles_total = sum(cycles) * world
+    total_s, cycles_total = aggregate_over_ranks(sum(ms) / 1e3, sum(cycles), world, dev)
     value = cycles_total / total_s
 
     # kernel launches of the timed binary64 steps, counted from the captured graphs

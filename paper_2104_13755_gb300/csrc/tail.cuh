@@ -98,14 +98,12 @@ struct TailThreads {
 };
 constexpr int kTailPre = 8;  // entries per lane held in registers
 
-// Split cluster barrier.  The release at arrive covers this thread's earlier
-// stores; loads of data that the phase does not write (matrix entries, b) may
-// be issued between arrive and wait, so their latency overlaps the barrier.
-__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
+// Cluster barrier with release / acquire ordering at cluster scope (the
+// non-.aligned form: a warp may reach it after divergent loops).  Separates
+// the phases other than the colour steps (copies, residual, restriction,
+// prolongation), which use the step mbarriers below.
 __device__ __forceinline__ void cluster_sync() {
-    cluster_arrive();
-    cluster_wait();
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
