@@ -577,17 +577,25 @@ void build_tail_table(smg_hierarchy* h, const LevelPlan& lp, DLevel& L, int cs, 
             }
         }
     }
+    // values a step barrier waits for: the colour's rows, plus one token from
+    // each CTA that has no unit in the colour
+    for (int r = 0; r < cs; r++) cfirst[r][nc] = n_my[r];
+    std::vector<int32_t> wait_vals(nc);
+    for (int c = 0; c < nc; c++) {
+        int empty = 0;
+        for (int r = 0; r < cs; r++) empty += cfirst[r][c + 1] == cfirst[r][c] ? 1 : 0;
+        wait_vals[c] = lp.colour_row[c + 1] - lp.colour_row[c] + empty;
+    }
     std::vector<int32_t> tab, off(cs + 1, 0);
     T.E_nmy.assign(cs, {0, 0});
     T.ints = 0;
     for (int r = 0; r < cs; r++) {
         off[r] = (int32_t)tab.size();
         const size_t head = tab.size();
-        cfirst[r][nc] = n_my[r];
         tab.push_back(n_my[r]);
         tab.push_back(E[r]);
         tab.insert(tab.end(), cfirst[r].begin(), cfirst[r].end());
-        for (int c = 0; c < nc; c++) tab.push_back(lp.colour_row[c + 1] - lp.colour_row[c]);
+        for (int c = 0; c < nc; c++) tab.push_back(wait_vals[c]);
         tab.insert(tab.end(), ent[r].begin(), ent[r].end());
         T.E_nmy[r] = {E[r], n_my[r]};
         T.ints = std::max(T.ints, (int)(tab.size() - head));

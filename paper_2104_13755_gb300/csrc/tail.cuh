@@ -32,8 +32,9 @@ namespace smg {
 // the CTAs and writes, per CTA, a table of its units, which the kernels copy to
 // shared memory at entry:
 //   [n_my, E] [cfirst: ncolours + 1] [rows: ncolours] [n_my x {off, W, row0, nrows, soff, g}]
-// (cfirst[c] = index of the CTA's first unit of colour c, rows[c] = rows of
-// colour c in the level, off = the slice's SELL offset, row0 / nrows = the
+// (cfirst[c] = index of the CTA's first unit of colour c, rows[c] = values a
+// step of colour c delivers to every replica: the colour's rows plus one token
+// from each CTA without a unit in it, off = the slice's SELL offset, row0 / nrows = the
 // unit's rows, E = sum W * 32 / R, soff = the unit's first entry in the staged
 // copy).  When the level is staged, the CTA also copies its units' column
 // indices, values, reciprocal diagonal and diagonal to shared memory, so a
@@ -209,6 +210,7 @@ struct LevelCtx {
     int n_my, nc, rlg, staged;
     uint32_t scol, sval, sdinv, sdiag;
     uint32_t bw;  // local copy of b (32 / R rows per unit)
+    uint32_t xr;  // this CTA's replica of x (shared::cta address of row 0)
     __device__ __forceinline__ int cfirst(int c) const { return lds_i(tab + 4u * (2 + c)); }
     __device__ __forceinline__ int rows(int c) const { return lds_i(tab + 4u * (3 + nc + c)); }
     // field f of work unit i: 0 SELL offset of its slice, 1 W, 2 first row, 3 rows, 4 staged offset,
@@ -231,16 +233,14 @@ __device__ __forceinline__ void st_async(uint32_t a, float v, uint32_t bar) {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(a), "f"(v), "r"(bar)
                  : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar_cluster) {
-    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive_expect_local(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.relaxed.cluster.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
 }
-// Wait for phase `parity` with acquire at cluster scope; bounded like mbar_wait.
-__device__ __forceinline__ void mbar_wait_cluster(uint32_t bar, uint32_t parity, int* err) {
-    if (err && *(volatile int*)err) return;  // an earlier wait gave up: do not wait again
+// Wait for phase `parity` with acquire at cluster scope, at most 2^22 polls; a
+// thread whose wait ran out sets *err and does not wait again (gave_up).
+__device__ __forceinline__ void mbar_wait_cluster(uint32_t bar, uint32_t parity, int* err, bool& gave_up) {
+    if (gave_up) return;
     for (int it = 0; it < (1 << 22); it++) {
         uint32_t done;
         asm volatile(
@@ -251,17 +251,22 @@ __device__ __forceinline__ void mbar_wait_cluster(uint32_t bar, uint32_t parity,
             : "memory");
         if (done) return;
     }
-    if (err) atomicExch(err, 1);
+    gave_up = true;
+    atomicExch(err, 1);
 }
 
-// Step barriers of the relaxation: two mbarriers (even and odd steps), each
-// completing when every CTA of the cluster has arrived for the step and the
-// step's new x values (every row of the colour, into this CTA's replica) have
-// landed.  A CTA arrives for step k only after finishing step k - 1, so no CTA
-// runs more than one step ahead of another and two barriers suffice.
+// Step barriers of the relaxation: two mbarriers (even and odd steps) per CTA,
+// each with one arrival (the CTA's own, announcing the step's byte count) and
+// completing when the step's values have landed in this CTA: every row of the
+// colour (into the replica of x) and one token from each CTA without a unit
+// in the colour.  Every CTA thus sends something in every step, and only after
+// its wait for the step before, so no CTA can reach step k + 2 (whose values
+// count on the same barrier as step k) before every CTA has passed step k:
+// two barriers suffice.
 struct StepBars {
     uint32_t bar0;  // shared::cta address of the even-step mbarrier (the odd one follows)
     uint32_t step;  // steps taken so far in this launch
+    bool gave_up;   // a wait of this thread ran out
     __device__ __forceinline__ uint32_t bar() const { return bar0 + 8u * (step & 1u); }
     __device__ __forceinline__ uint32_t parity() const { return (step >> 1) & 1u; }
 };
@@ -293,6 +298,7 @@ __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const
     C.sdinv = st + lay.dinv;
     C.sdiag = st + lay.diag;
     C.bw = D.template rep<T, K>(L.sbase + L.npad + 2 * L.nloc, 0);
+    C.xr = D.template rep<T, K>(L.sbase, 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rl_lg = 5 - C.rlg, RL = 1 << rl_lg;  // rows per unit
     for (int i = warp; i < C.n_my; i += TailThreads<T>::warps) {
@@ -386,7 +392,7 @@ struct TailRows {
             if (k < W) {
                 const int c = col_at(C, k);
                 v[u] = val_at(C, k);
-                xa[u] = D.template rep<T, K>(L.sbase, c);
+                xa[u] = C.xr + (uint32_t)(c * K * (int)sizeof(T));
             }
         }
         if (staged) d = lds<T>((RESIDUAL ? C.sdiag : C.sdinv) + (uint32_t)sizeof(T) * ((i << rl_lg) + r));
@@ -394,7 +400,7 @@ struct TailRows {
         const uint32_t ba = C.bw + (uint32_t)((((i << rl_lg) + r) * K) * (int)sizeof(T));
 #pragma unroll
         for (int q = 0; q < K; q++) bb[q] = lds<T>(ba + q * (int)sizeof(T));
-        xrow = D.template rep<T, K>(L.sbase, row);
+        xrow = C.xr + (uint32_t)(row * K * (int)sizeof(T));
         if (RESIDUAL) rself = D.template at<T, K>(L.sbase + L.npad + L.nloc, row);
     }
 
@@ -409,27 +415,28 @@ struct TailRows {
             if (sub + (u << rlg) < W)
 #pragma unroll
                 for (int q = 0; q < K; q++) xv[u][q] = lds<T>(xa[u] + q * (int)sizeof(T));
-        T a0[K], a1[K];
+        // one chain per lane: every binary64 instruction holds the warp for the
+        // same time whether or not it depends on the previous one, so fewer
+        // instructions, not shorter chains, shorten a step; for Gauss-Seidel the
+        // row's first lane starts from b
+        T a0[K];
 #pragma unroll
-        for (int q = 0; q < K; q++) a0[q] = a1[q] = T(0);
+        for (int q = 0; q < K; q++) a0[q] = (!RESIDUAL && sub == 0) ? bb[q] : T(0);
 #pragma unroll
         for (int u = 0; u < PRE; u++)
             if (sub + (u << rlg) < W)
 #pragma unroll
-                for (int q = 0; q < K; q++) {
-                    if (u & 1) a1[q] -= v[u] * xv[u][q];
-                    else a0[q] -= v[u] * xv[u][q];
-                }
+                for (int q = 0; q < K; q++) a0[q] -= v[u] * xv[u][q];
         for (int k = sub + (PRE << rlg); k < W; k += 1 << rlg) {  // rows longer than PRE * R
             const int c = col_at(C, k);
             const T vv = val_at(C, k);
-            const uint32_t a = D.template rep<T, K>(C.L->sbase, c);
+            const uint32_t a = C.xr + (uint32_t)(c * K * (int)sizeof(T));
 #pragma unroll
             for (int q = 0; q < K; q++) a0[q] -= vv * lds<T>(a + q * (int)sizeof(T));
         }
         T acc[K];
 #pragma unroll
-        for (int q = 0; q < K; q++) acc[q] = a0[q] + a1[q];
+        for (int q = 0; q < K; q++) acc[q] = a0[q];
         for (int o = 16; o >= (32 >> rlg); o >>= 1)  // every lane of the row ends with the sum
 #pragma unroll
             for (int q = 0; q < K; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
@@ -442,7 +449,7 @@ struct TailRows {
         } else {
             T out[K];
 #pragma unroll
-            for (int q = 0; q < K; q++) out[q] = (bb[q] + acc[q]) * d;
+            for (int q = 0; q < K; q++) out[q] = acc[q] * d;  // (b - sum a x) / a_rr
             const int cs = 1 << D.lg;
             for (int j = sub; j < cs; j += 1 << rlg) {  // the row's lanes share the CS replica writes
                 const uint32_t a = dsm(xrow, (uint32_t)j);
@@ -454,16 +461,20 @@ struct TailRows {
     }
 };
 
+// Landing slot of the tokens (same offset in every CTA; never read).
+__shared__ __align__(8) double tail_token[4];
+
 // Gauss-Seidel over the colour sequence of `steps` steps (colour of step k from
 // col_of(k)).  New values go to every replica by st.async, counted on the
-// receivers' step barriers; each CTA then arrives for the step on every CTA's
-// barrier (its own with the step's byte count: all rows of the colour), loads
-// its next step's entries and waits.  The loop ends with a cluster barrier, so
-// no store or arrival of the relaxation is in flight afterwards.
+// receivers' step barriers (a CTA without a unit in the colour sends its
+// token instead); each CTA then arrives on its own barrier with the step's
+// byte count, loads its next step's entries and waits.  The loop ends with a
+// cluster barrier, so no store of the relaxation is in flight afterwards.
 template <typename T, int K, class ColourOf>
 __device__ __forceinline__ void tail_relax(const LevelCtx<T>& C, const Dist& D, int steps, ColourOf col_of,
                                            int warp, int lane, StepBars& sb) {
     TailRows<T, K> cur;
+    const uint32_t tok = (uint32_t)__cvta_generic_to_shared(tail_token);
     auto load = [&](int c, int u) {
         const int i = C.cfirst(c) + u;
         cur.template load<false>(C, D, i < C.cfirst(c + 1) ? i : -1, lane);
@@ -478,15 +489,15 @@ __device__ __forceinline__ void tail_relax(const LevelCtx<T>& C, const Dist& D, 
             load(c, u);
             cur.template run<false>(C, D, bar);
         }
-        if (warp == 0 && lane < (1 << D.lg)) {
-            if ((uint32_t)lane == D.rank) {
-                mbar_arrive_expect_local(bar, (uint32_t)C.rows(c) * (uint32_t)(K * sizeof(T)));
-            } else {
-                mbar_arrive_remote(dsm(bar, (uint32_t)lane));
-            }
+        if (warp == 0) {
+            if (units == 0 && lane < (1 << D.lg))  // no unit in this colour: a token to every CTA
+#pragma unroll
+                for (int q = 0; q < K; q++)
+                    st_async(dsm(tok + q * (uint32_t)sizeof(T), (uint32_t)lane), T(0), dsm(bar, (uint32_t)lane));
+            if (lane == 0) mbar_arrive_expect_local(bar, (uint32_t)C.rows(c) * (uint32_t)(K * sizeof(T)));
         }
         if (k + 1 < steps) load(col_of(k + 1), warp);
-        mbar_wait_cluster(bar, sb.parity(), C.L->err);
+        mbar_wait_cluster(bar, sb.parity(), C.L->err, sb.gave_up);
         sb.step++;
     }
     cluster_sync();
@@ -624,10 +635,10 @@ __global__ void __launch_bounds__(TailThreads<T>::value, 1) tail_down(const Tail
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ __align__(8) unsigned long long mbar[2];  // step barriers: even, odd steps
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
-    StepBars sb{bar, 0u};
+    StepBars sb{bar, 0u, false};
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1 << lg);
-        mbar_init(bar + 8u, 1 << lg);
+        mbar_init(bar, 1);
+        mbar_init(bar + 8u, 1);
     }
     pdl_wait();
     pdl_trigger();
@@ -655,10 +666,10 @@ __global__ void __launch_bounds__(TailThreads<T>::value, 1) tail_up(const TailLe
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ __align__(8) unsigned long long mbar[2];  // step barriers: even, odd steps
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
-    StepBars sb{bar, 0u};
+    StepBars sb{bar, 0u, false};
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1 << lg);
-        mbar_init(bar + 8u, 1 << lg);
+        mbar_init(bar, 1);
+        mbar_init(bar + 8u, 1);
     }
     pdl_wait();
     pdl_trigger();
