@@ -23,20 +23,22 @@ __global__ void k_pad_copy(const double* __restrict__ A, int64_t n, double* __re
     X[e] = (i == j) ? 1.0 : 0.0;
 }
 
-// Factor diagonal tile j.  Binary64 FMA issue is about one lane per two clocks
-// per SM sub-partition, so the work is spread over the four sub-partitions:
-// warp w holds columns c = w, w + 4, ... of the tile in registers (lane = row).
-// Per pivot k the warp owning column k takes the pivot by shuffle, CUDA's
-// binary64 rsqrt gives 1 / sqrt(pivot), its lanes scale column k and publish it
-// in shared memory (two buffers, so one barrier per pivot), and every warp
-// applies the rank-1 update to its columns right of k (lower triangle).
-constexpr int kDiagWarps = 4;
+// Factor diagonal tile j.  A binary64 instruction holds its warp for about 64
+// clocks on this part (dependent or not), so the pivot chain (shuffle, CUDA's
+// binary64 rsqrt, scale) sets the time and everything else is kept off it:
+// warp w holds columns c = w, w + 8, ... of the tile in registers (lane = row);
+// in step k the owner of column k + 1 applies pivot k to that column only,
+// factors it (pivot k + 1) and publishes it in shared memory, while every other
+// warp applies pivot k to its columns right of k + 1 (lower triangle).  The
+// owner catches up on pivot k in step k + 1, so the published columns rotate
+// over three buffers and one barrier per pivot suffices.
+constexpr int kDiagWarps = 8;
 constexpr int kDiagCols = NB / kDiagWarps;
 __global__ void __launch_bounds__(32 * kDiagWarps) k_chol_diag(double* __restrict__ C, int64_t np, int j,
                                                                 double* __restrict__ rinv_out,
                                                                 int32_t* __restrict__ bad) {
     __shared__ double a[NB][NB + 1];
-    __shared__ double lk[2][NB];
+    __shared__ double lk[3][NB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double* T = C + (int64_t)j * NB * np + (int64_t)j * NB;
     for (int e = threadIdx.x; e < NB * NB; e += 32 * kDiagWarps) a[e / NB][e % NB] = T[(int64_t)(e / NB) * np + e % NB];
@@ -45,28 +47,41 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_chol_diag(double* __restric
 #pragma unroll
     for (int m = 0; m < kDiagCols; m++) col[m] = a[lane][m * kDiagWarps + w];
     bool flagged = false;
+    // column p (owned by this warp, slot mp) becomes column p of L
+    auto pivot = [&](double& cp, int p) {
+        double d = __shfl_sync(0xffffffffu, cp, p);
+        if (!(d > 0.0) || !isfinite(d)) {  // not SPD: flag it, keep the arithmetic finite
+            flagged = true;
+            d = 1.0;
+        }
+        const double y = rsqrt(d);
+        const double l = (lane == p) ? d * y : cp * y;
+        if (lane >= p) cp = l;
+        lk[p % 3][lane] = l;
+        if (lane == p) rinv_out[(int64_t)j * NB + p] = y;
+    };
+    if (w == 0) pivot(col[0], 0);
+    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NB; k++) {
-        const int mk = k / kDiagWarps;
-        if (w == k % kDiagWarps) {
-            double d = __shfl_sync(0xffffffffu, col[mk], k);
-            if (!(d > 0.0) || !isfinite(d)) {  // not SPD: flag it, keep the arithmetic finite
-                flagged = true;
-                d = 1.0;
+    for (int k = 0; k + 1 < NB; k++) {
+        const double lr = lk[k % 3][lane];
+        if (w == (k + 1) % kDiagWarps) {
+            const int m1 = (k + 1) / kDiagWarps;
+            if (lane >= k + 1) col[m1] -= lr * lk[k % 3][k + 1];
+            pivot(col[m1], k + 1);
+        } else {
+            const bool late = k > 0 && w == k % kDiagWarps;  // owner of column k: pivot k - 1 still to apply
+            const double lp = late ? lk[(k + 2) % 3][lane] : 0.0;
+#pragma unroll
+            for (int m = 0; m < kDiagCols; m++) {
+                const int c = m * kDiagWarps + w;
+                if (c > k + 1 && lane >= c) {
+                    if (late) col[m] -= lp * lk[(k + 2) % 3][c];
+                    col[m] -= lr * lk[k % 3][c];
+                }
             }
-            const double y = rsqrt(d);
-            const double l = (lane == k) ? d * y : col[mk] * y;
-            if (lane >= k) col[mk] = l;
-            lk[k & 1][lane] = l;
-            if (lane == k) rinv_out[(int64_t)j * NB + k] = y;
         }
         __syncthreads();
-        const double lr = lk[k & 1][lane];
-#pragma unroll
-        for (int m = 0; m < kDiagCols; m++) {
-            const int c = m * kDiagWarps + w;
-            if (c > k && lane >= c) col[m] -= lr * lk[k & 1][c];
-        }
     }
     if (flagged) atomicExch(bad, 1);
 #pragma unroll
@@ -77,8 +92,10 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_chol_diag(double* __restric
 }
 
 // Inverse of diagonal tile j (X = L_jj^{-1}, forward elimination of L X = I):
-// columns are independent, so kQ blocks of four warps take two columns per
-// warp; lane = row, the row-k value of a column arrives by shuffle.
+// columns are independent, so eight blocks of four warps take one column per
+// warp (each binary64 instruction holds its warp, so one column per warp is
+// the shortest chain); lane = row, the row-k value arrives by shuffle.
+constexpr int kInvBlocks = NB / 4;
 __global__ void __launch_bounds__(128) k_tile_inv(const double* __restrict__ C, int64_t np, int j,
                                                   const double* __restrict__ rinv, double* __restrict__ dblk) {
     __shared__ double l[NB][NB + 1];
@@ -86,24 +103,16 @@ __global__ void __launch_bounds__(128) k_tile_inv(const double* __restrict__ C, 
     const double* T = C + (int64_t)j * NB * np + (int64_t)j * NB;
     for (int e = threadIdx.x; e < NB * NB; e += 128) l[e / NB][e % NB] = T[(int64_t)(e / NB) * np + e % NB];
     __syncthreads();
-    const int c0 = blockIdx.x * 8 + w * 2;  // this warp's two columns
-    double x0 = (lane == c0) ? 1.0 : 0.0, x1 = (lane == c0 + 1) ? 1.0 : 0.0;
+    const int c0 = blockIdx.x * 4 + w;  // this warp's column
+    double x0 = (lane == c0) ? 1.0 : 0.0;
     const double ri = rinv[(int64_t)j * NB + lane];
     for (int k = c0; k < NB; k++) {
-        // row k of both columns is final after scaling; broadcast it
+        // row k of the column is final after scaling; broadcast it
         const double k0 = __shfl_sync(0xffffffffu, x0 * ri, k);
-        const double k1 = __shfl_sync(0xffffffffu, x1 * ri, k);
-        if (lane == k) {
-            x0 = k0;
-            x1 = k1;
-        } else if (lane > k) {
-            const double lrk = l[lane][k];
-            x0 -= lrk * k0;
-            x1 -= lrk * k1;
-        }
+        if (lane == k) x0 = k0;
+        else if (lane > k) x0 -= l[lane][k] * k0;
     }
     dblk[(int64_t)j * NB * NB + lane * NB + c0] = (lane >= c0) ? x0 : 0.0;
-    dblk[(int64_t)j * NB * NB + lane * NB + c0 + 1] = (lane >= c0 + 1) ? x1 : 0.0;
 }
 
 // Work units of the tile kernels: a 32 x 32 output tile split into kQ blocks of
@@ -308,7 +317,7 @@ void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s) {
     bool forked3 = false;  // s3 joins the captured work only once it has some
     for (int j = 0; j < nb; j++) {
         k_chol_diag<<<1, 32 * kDiagWarps, 0, s>>>(C.chol, np, j, C.rinv, &h->state->chol_bad);
-        k_tile_inv<<<kQ, 128, 0, s>>>(C.chol, np, j, C.rinv, C.dblk);
+        k_tile_inv<<<kInvBlocks, 128, 0, s>>>(C.chol, np, j, C.rinv, C.dblk);
         const int T = nb - j - 1;
         if (T > 0) k_chol_panel<<<T * kQ, kQR * NB, 0, s>>>(C.chol, np, j, C.dblk);
         cudaEventRecord(h->ev_step[j], s);

@@ -85,19 +85,35 @@ struct RowSlice {
     template <bool COHERENT = false>
     __device__ __forceinline__ void dot(const SliceMeta& m, const int32_t* __restrict__ col,
                                         const T* __restrict__ sval, const T* x, T (&acc)[K]) const {
+        T zero[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) zero[q] = T(0);
+        dot_from<COHERENT>(m, col, sval, x, zero, acc);
+    }
+    // acc = init - sum_k a_k x_{c_k}: the row's first lane starts its chain
+    // from init, so the caller's own term costs no separate add.
+    template <bool COHERENT = false>
+    __device__ __forceinline__ void dot_from(const SliceMeta& m, const int32_t* __restrict__ col,
+                                             const T* __restrict__ sval, const T* x, const T (&init)[K],
+                                             T (&acc)[K]) const {
         T xv[PRE][K];
 #pragma unroll
         for (int u = 0; u < PRE; u++)
             if (sub + R * u < W)
 #pragma unroll
                 for (int q = 0; q < K; q++) xv[u][q] = ldx<COHERENT>(x + (int64_t)c[u] * K + q);
-        // With several lanes per row (latency-bound levels) two independent FMA
-        // chains shorten the dependent binary64 chain; with one lane per row
-        // (the finest level, bound by FP64 issue) one chain saves the extra add.
-        constexpr bool SPLIT = R > 1;
+        // Binary64: one chain.  A binary64 instruction holds its warp for the
+        // same ~64 clocks whether or not it depends on the one before, so the
+        // count of instructions, not the chain depth, sets the time; a second
+        // chain would only add the final add.  Binary32 with several lanes per
+        // row: two chains for instruction-level parallelism.
+        constexpr bool SPLIT = R > 1 && sizeof(T) == 4;
         T a1[K];
 #pragma unroll
-        for (int q = 0; q < K; q++) acc[q] = a1[q] = T(0);
+        for (int q = 0; q < K; q++) {
+            acc[q] = sub == 0 ? init[q] : T(0);
+            a1[q] = T(0);
+        }
 #pragma unroll
         for (int u = 0; u < PRE; u++)
             if (sub + R * u < W)
@@ -145,11 +161,13 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) gs_colour(co
     const T d = dinv[row];
     pdl_wait();
     pdl_trigger();
-    T acc[K];
-    rs.dot(m, col, sval, x, acc);
+    T bv[K], acc[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) bv[q] = b[(int64_t)row * K + q];
+    rs.dot_from(m, col, sval, x, bv, acc);  // b_i - sum_{j != i} a_ij x_j
     if (valid && rs.sub == 0)
 #pragma unroll
-        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = (b[(int64_t)row * K + q] + acc[q]) * d;
+        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = acc[q] * d;
 }
 
 // Damped Jacobi update x <- x + omega D^{-1} r after r = b - A x (App.
@@ -183,12 +201,13 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) residual(con
     const T d = diag[row];
     pdl_wait();
     pdl_trigger();
-    T acc[K];
-    rs.dot(m, col, sval, x, acc);
+    T own[K], acc[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) own[q] = b[(int64_t)row * K + q] - d * x[(int64_t)row * K + q];
+    rs.dot_from(m, col, sval, x, own, acc);  // b_i - a_ii x_i - sum_{j != i} a_ij x_j
     if (valid && rs.sub == 0)
 #pragma unroll
-        for (int q = 0; q < K; q++)
-            r[(int64_t)row * K + q] = (b[(int64_t)row * K + q] - d * x[(int64_t)row * K + q]) + acc[q];
+        for (int q = 0; q < K; q++) r[(int64_t)row * K + q] = acc[q];
 }
 
 // Restriction r_{h+1} = P^T r_h (Alg. 2 "restrict residual") through the CSR of
@@ -289,18 +308,23 @@ __global__ void __launch_bounds__(kThreads) resnorm(const SliceMeta* __restrict_
         const SliceMeta m = slices[w / R];
         RowSlice<double, K, R, Pre<double, K, R>::value> rs;
         rs.load(m, w % R, lane, col, sval);
-        double acc[K];
-        rs.dot(m, col, sval, x, acc);
-        if (rs.r < m.nrows && rs.sub == 0) {
-            const int row = m.row0 + rs.r;
-            const double d = diag[row];
+        const bool valid = rs.r < m.nrows;
+        const int row = m.row0 + (valid ? rs.r : 0);
+        const double d = diag[row];
+        double bv[K], own[K], acc[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            bv[q] = b[(int64_t)row * K + q];
+            own[q] = bv[q] - d * x[(int64_t)row * K + q];
+        }
+        rs.dot_from(m, col, sval, x, own, acc);  // the residual of the row
+        if (valid && rs.sub == 0) {
 #pragma unroll
             for (int q = 0; q < K; q++) {
-                const double bv = b[(int64_t)row * K + q];
-                const double rv = (bv - d * x[(int64_t)row * K + q]) + acc[q];
+                const double rv = acc[q];
                 rr[q] += rv * rv;
                 if (r64) r64[(int64_t)row * K + q] = rv;
-                if (INIT) bb[q] += bv * bv;
+                if (INIT) bb[q] += bv[q] * bv[q];
                 if (R32) {
                     r32[(int64_t)row * K + q] = (float)rv;
                     x32[(int64_t)row * K + q] = 0.0f;

@@ -417,11 +417,14 @@ struct TailRows {
                 for (int q = 0; q < K; q++) xv[u][q] = lds<T>(xa[u] + q * (int)sizeof(T));
         // one chain per lane: every binary64 instruction holds the warp for the
         // same time whether or not it depends on the previous one, so fewer
-        // instructions, not shorter chains, shorten a step; for Gauss-Seidel the
-        // row's first lane starts from b
+        // instructions, not shorter chains, shorten a step; the row's first lane
+        // starts from b (Gauss-Seidel) or b - a_rr x_r (residual)
         T a0[K];
 #pragma unroll
-        for (int q = 0; q < K; q++) a0[q] = (!RESIDUAL && sub == 0) ? bb[q] : T(0);
+        for (int q = 0; q < K; q++) {
+            a0[q] = T(0);
+            if (sub == 0) a0[q] = RESIDUAL ? bb[q] - d * lds<T>(xrow + q * (int)sizeof(T)) : bb[q];
+        }
 #pragma unroll
         for (int u = 0; u < PRE; u++)
             if (sub + (u << rlg) < W)
@@ -445,7 +448,7 @@ struct TailRows {
             if (sub == 0)
 #pragma unroll
                 for (int q = 0; q < K; q++)
-                    stc(rself + q * (int)sizeof(T), (bb[q] - d * lds<T>(xrow + q * (int)sizeof(T))) + acc[q]);
+                    stc(rself + q * (int)sizeof(T), acc[q]);
         } else {
             T out[K];
 #pragma unroll
