@@ -46,16 +46,13 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_chol_diag(double* __restric
     double col[kDiagCols];  // col[m] = a[lane][m * kDiagWarps + w]
 #pragma unroll
     for (int m = 0; m < kDiagCols; m++) col[m] = a[lane][m * kDiagWarps + w];
-    bool flagged = false;
-    // column p (owned by this warp, slot mp) becomes column p of L
+    // column p (owned by this warp) becomes column p of L: l = a / sqrt(a_pp),
+    // on lane p itself sqrt(a_pp).  No test on the pivot chain: a pivot that is
+    // not positive gives a NaN or an infinity that the check of the diagonal
+    // after the loop reports.
     auto pivot = [&](double& cp, int p) {
-        double d = __shfl_sync(0xffffffffu, cp, p);
-        if (!(d > 0.0) || !isfinite(d)) {  // not SPD: flag it, keep the arithmetic finite
-            flagged = true;
-            d = 1.0;
-        }
-        const double y = rsqrt(d);
-        const double l = (lane == p) ? d * y : cp * y;
+        const double y = rsqrt(__shfl_sync(0xffffffffu, cp, p));
+        const double l = cp * y;
         if (lane >= p) cp = l;
         lk[p % 3][lane] = l;
         if (lane == p) rinv_out[(int64_t)j * NB + p] = y;
@@ -83,12 +80,14 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_chol_diag(double* __restric
         }
         __syncthreads();
     }
-    if (flagged) atomicExch(bad, 1);
+    bool flagged = false;  // not SPD: a diagonal entry of L that is not positive and finite
 #pragma unroll
     for (int m = 0; m < kDiagCols; m++) {
         const int c = m * kDiagWarps + w;
+        if (lane == c && !(col[m] > 0.0 && isfinite(col[m]))) flagged = true;
         T[(int64_t)lane * np + c] = (c <= lane) ? col[m] : 0.0;
     }
+    if (flagged) atomicExch(bad, 1);
 }
 
 // Inverse of diagonal tile j (X = L_jj^{-1}, forward elimination of L X = I):
