@@ -235,12 +235,17 @@ __global__ void k_coarse_lower(const double* __restrict__ X, int64_t np, int n, 
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
+    const double* row = X + (int64_t)i * np;
+    // the factor does not change within a cycle: pull the row into L2 while the
+    // grid waits for its predecessor (launched early, it waits through the
+    // whole down-sweep below)
+    for (int c = lane * 16; c <= i; c += 32 * 16) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + c));
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     double acc[K];
 #pragma unroll
     for (int q = 0; q < K; q++) acc[q] = 0.0;
-    const double* row = X + (int64_t)i * np;
+#pragma unroll 8
     for (int j = lane; j <= i; j += 32) {
         double xv = row[j];
 #pragma unroll
@@ -263,12 +268,14 @@ __global__ void k_coarse_upper(const double* __restrict__ XT, int64_t np, int n,
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
+    const double* row = XT + (int64_t)j * np;
+    for (int c = (j & ~15) + lane * 16; c < n; c += 32 * 16) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + c));
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     double acc[K];
 #pragma unroll
     for (int q = 0; q < K; q++) acc[q] = 0.0;
-    const double* row = XT + (int64_t)j * np;
+#pragma unroll 8
     for (int i = j + lane; i < n; i += 32) {
         double xv = row[i];
 #pragma unroll

@@ -173,6 +173,18 @@ __device__ __forceinline__ void sts_i(uint32_t a, int v) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
+// Asynchronous global -> shared copies (4, 8 or 16 bytes, both addresses
+// aligned to the size), all in flight together until cp_async_wait_all().
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes) {
+    if (bytes == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    else if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Rows over the CS = 1 << lg CTAs of the cluster (distributed arrays) and the
 // local replicas.
 struct Dist {
@@ -301,44 +313,45 @@ __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const
     C.xr = D.template rep<T, K>(L.sbase, 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rl_lg = 5 - C.rlg, RL = 1 << rl_lg;  // rows per unit
-    for (int i = warp; i < C.n_my; i += TailThreads<T>::warps) {
-        const int off = C.unit(i, 0), W = C.unit(i, 1), row0 = C.unit(i, 2), nrows = C.unit(i, 3);
-        const int soff = C.unit(i, 4), g = C.unit(i, 5);
-        if (C.staged) {  // entries (k, rl) of the unit's rows, unit-major: staged index soff + k * RL + rl
-            const int n = W << rl_lg;
-            for (int e0 = 0; e0 < n; e0 += 32 * 4) {
-                int cv[4];
-                T vv[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int e = e0 + 32 * u + lane;
-                    if (e < n) {
-                        const int src = off + (e >> rl_lg) * 32 + g * RL + (e & (RL - 1));
-                        cv[u] = __ldg(L.col + src);
-                        vv[u] = __ldg(L.sval + src);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int e = e0 + 32 * u + lane;
-                    if (e < n) {
-                        sts_i(C.scol + 4u * (soff + e), cv[u]);
-                        sts(C.sval + (uint32_t)sizeof(T) * (soff + e), vv[u]);
-                    }
-                }
+    if (C.staged) {
+        // entries (k, rl) of a unit's rows, unit-major: staged index soff + k * RL + rl.  Per k the
+        // unit's RL column indices and values are contiguous in the SELL arrays (and RL-aligned), so
+        // they move as a few 4-16 byte asynchronous copies, all of the CTA's in flight together.
+        const bool a16 = ((reinterpret_cast<uintptr_t>(L.col) | reinterpret_cast<uintptr_t>(L.sval)) & 15u) == 0;
+        const int cb = RL * 4, cps = !a16 ? 4 : (cb < 16 ? cb : 16), cpn = cb / cps;
+        const int vb = RL * (int)sizeof(T), vps = !a16 ? (int)sizeof(T) : (vb < 16 ? vb : 16), vpn = vb / vps;
+        const int per = cpn + vpn;
+        for (int i = warp; i < C.n_my; i += TailThreads<T>::warps) {
+            const int off = C.unit(i, 0), W = C.unit(i, 1), soff = C.unit(i, 4), g = C.unit(i, 5);
+            for (int t = lane; t < W * per; t += 32) {
+                const int k = t / per, p = t - k * per;
+                const int src = off + k * 32 + g * RL, dst = soff + k * RL;
+                if (p < cpn)
+                    cp_async(C.scol + 4u * dst + (uint32_t)(p * cps), (const char*)(L.col + src) + p * cps, cps);
+                else
+                    cp_async(C.sval + (uint32_t)sizeof(T) * dst + (uint32_t)((p - cpn) * vps),
+                             (const char*)(L.sval + src) + (p - cpn) * vps, vps);
             }
-        }
-        if (lane < nrows) {
-            if (C.staged) {
-                sts(C.sdinv + (uint32_t)sizeof(T) * ((i << rl_lg) + lane), L.dinv[row0 + lane]);
-                sts(C.sdiag + (uint32_t)sizeof(T) * ((i << rl_lg) + lane), L.diag[row0 + lane]);
-            }
-            const uint32_t src = D.template at<T, K>(L.sbase + L.npad, row0 + lane);
-#pragma unroll
-            for (int q = 0; q < K; q++)
-                sts(C.bw + (((i << rl_lg) + lane) * K + q) * (int)sizeof(T), ldc<T>(src + q * (int)sizeof(T)));
         }
     }
+    // per unit row: reciprocal diagonal and diagonal (staged), b from the distributed array;
+    // one thread per row so the remote loads are all in flight together
+    for (int t = threadIdx.x; t < (C.n_my << rl_lg); t += TailThreads<T>::value) {
+        const int i = t >> rl_lg, r = t & (RL - 1);
+        if (r >= C.unit(i, 3)) continue;
+        const int row = C.unit(i, 2) + r;
+        if (C.staged) {
+            cp_async(C.sdinv + (uint32_t)sizeof(T) * t, L.dinv + row, (int)sizeof(T));
+            cp_async(C.sdiag + (uint32_t)sizeof(T) * t, L.diag + row, (int)sizeof(T));
+        }
+        const uint32_t src = D.template at<T, K>(L.sbase + L.npad, row);
+        T bv[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) bv[q] = ldc<T>(src + q * (int)sizeof(T));
+#pragma unroll
+        for (int q = 0; q < K; q++) sts(C.bw + (uint32_t)((t * K + q) * (int)sizeof(T)), bv[q]);
+    }
+    cp_async_wait_all();
     __syncthreads();
     return C;
 }
@@ -596,10 +609,20 @@ __device__ __forceinline__ void tail_prolong(const TailLevel<T>& L, const TailLe
     }
 }
 
-// Global x of a level into this CTA's replica (all rows).
+// Global x of a level into this CTA's replica (all rows): 16-byte asynchronous
+// copies where both sides are aligned, single values otherwise.  Completes
+// before return (CTA-local; the caller's barrier publishes it).
 template <typename T, int K>
 __device__ __forceinline__ void tail_load_x(const TailLevel<T>& L, const Dist& D) {
-    for (int e = threadIdx.x; e < L.n * K; e += TailThreads<T>::value) sts(D.template rep<T, 1>(L.sbase * K, e), L.x[e]);
+    const uint32_t dst = D.template rep<T, 1>(L.sbase * K, 0);
+    const int bytes = L.n * K * (int)sizeof(T);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(L.x) | dst) & 15u) == 0;
+    const int chunks = aligned ? bytes / 16 : 0;
+    for (int c = threadIdx.x; c < chunks; c += TailThreads<T>::value)
+        cp_async(dst + 16u * c, (const char*)L.x + 16 * c, 16);
+    for (int e = chunks * 16 / (int)sizeof(T) + threadIdx.x; e < L.n * K; e += TailThreads<T>::value)
+        cp_async(dst + (uint32_t)(e * (int)sizeof(T)), L.x + e, (int)sizeof(T));
+    cp_async_wait_all();
 }
 
 // This CTA's rows of b between global memory and the distributed array, and
