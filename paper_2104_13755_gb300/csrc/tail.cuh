@@ -293,7 +293,8 @@ __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const
     const TailLevel<T>& L = *Lp;
     const uint32_t sm = (uint32_t)__cvta_generic_to_shared(tail_smem()) + (uint32_t)L.rbase;
     const int t0 = L.table_off[D.rank], t1 = L.table_off[D.rank + 1];
-    for (int e = threadIdx.x; e < t1 - t0; e += TailThreads<T>::value) sts_i(sm + 4u * e, L.table[t0 + e]);
+    for (int e = threadIdx.x; e < t1 - t0; e += TailThreads<T>::value) cp_async(sm + 4u * e, L.table + t0 + e, 4);
+    cp_async_wait_all();
     __syncthreads();
     LevelCtx<T> C;
     C.L = Lp;
@@ -519,9 +520,40 @@ __device__ __forceinline__ void tail_relax(const LevelCtx<T>& C, const Dist& D, 
     cluster_sync();
 }
 
-// r = b - A x over all rows (this CTA's slices of every colour).
+// r = b - A x over all rows (this CTA's units of every colour).  With the
+// entries staged, one thread per row: no colour order to respect here, and a
+// lane that walks its row needs one binary64 instruction per entry instead of
+// the entries over R lanes plus the log R reduction steps, so the step, which
+// binary64 issue bounds, takes about half the instructions.
 template <typename T, int K>
 __device__ __forceinline__ void tail_residual(const LevelCtx<T>& C, const Dist& D, int warp, int lane) {
+    if (C.staged) {
+        const TailLevel<T>& L = *C.L;
+        const int rl_lg = 5 - C.rlg, RL = 1 << rl_lg;
+        for (int t = threadIdx.x; t < (C.n_my << rl_lg); t += TailThreads<T>::value) {
+            const int i = t >> rl_lg, r = t & (RL - 1);
+            if (r >= C.unit(i, 3)) continue;
+            const int W = C.unit(i, 1), soff = C.unit(i, 4), row = C.unit(i, 2) + r;
+            const T d = lds<T>(C.sdiag + (uint32_t)sizeof(T) * t);
+            const uint32_t xrow = C.xr + (uint32_t)(row * K * (int)sizeof(T));
+            T acc[K];
+#pragma unroll
+            for (int q = 0; q < K; q++)
+                acc[q] = lds<T>(C.bw + (uint32_t)((t * K + q) * (int)sizeof(T))) - d * lds<T>(xrow + q * (int)sizeof(T));
+#pragma unroll 4
+            for (int k = 0; k < W; k++) {
+                const int e = soff + k * RL + r;
+                const uint32_t xa = C.xr + (uint32_t)(lds_i(C.scol + 4u * e) * K * (int)sizeof(T));
+                const T v = lds<T>(C.sval + (uint32_t)sizeof(T) * e);
+#pragma unroll
+                for (int q = 0; q < K; q++) acc[q] -= v * lds<T>(xa + q * (int)sizeof(T));
+            }
+            const uint32_t rs = D.template at<T, K>(L.sbase + L.npad + L.nloc, row);
+#pragma unroll
+            for (int q = 0; q < K; q++) stc(rs + q * (int)sizeof(T), acc[q]);
+        }
+        return;
+    }
     TailRows<T, K> cur;
     for (int u = warp; u < C.n_my; u += TailThreads<T>::warps) {
         cur.template load<true>(C, D, u, lane);
