@@ -321,17 +321,15 @@ __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const
         const bool a16 = ((reinterpret_cast<uintptr_t>(L.col) | reinterpret_cast<uintptr_t>(L.sval)) & 15u) == 0;
         const int cb = RL * 4, cps = !a16 ? 4 : (cb < 16 ? cb : 16), cpn = cb / cps;
         const int vb = RL * (int)sizeof(T), vps = !a16 ? (int)sizeof(T) : (vb < 16 ? vb : 16), vpn = vb / vps;
-        const int per = cpn + vpn;
         for (int i = warp; i < C.n_my; i += TailThreads<T>::warps) {
             const int off = C.unit(i, 0), W = C.unit(i, 1), soff = C.unit(i, 4), g = C.unit(i, 5);
-            for (int t = lane; t < W * per; t += 32) {
-                const int k = t / per, p = t - k * per;
+            for (int k = lane; k < W; k += 32) {  // one k of the unit per lane: its RL indices and values
                 const int src = off + k * 32 + g * RL, dst = soff + k * RL;
-                if (p < cpn)
-                    cp_async(C.scol + 4u * dst + (uint32_t)(p * cps), (const char*)(L.col + src) + p * cps, cps);
-                else
-                    cp_async(C.sval + (uint32_t)sizeof(T) * dst + (uint32_t)((p - cpn) * vps),
-                             (const char*)(L.sval + src) + (p - cpn) * vps, vps);
+                const char* sc = (const char*)(L.col + src);
+                const char* sv = (const char*)(L.sval + src);
+                const uint32_t dc = C.scol + 4u * dst, dv = C.sval + (uint32_t)sizeof(T) * dst;
+                for (int p = 0; p < cpn; p++) cp_async(dc + (uint32_t)(p * cps), sc + p * cps, cps);
+                for (int p = 0; p < vpn; p++) cp_async(dv + (uint32_t)(p * vps), sv + p * vps, vps);
             }
         }
     }
