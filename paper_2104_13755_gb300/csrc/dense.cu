@@ -202,22 +202,30 @@ __global__ void __launch_bounds__(NB * NB) k_trinv_row(double* __restrict__ X, i
 
 // B_k,jb -= L_k,i X_i,jb for k > i, jb <= i (output rows split over kQ blocks;
 // the tiles read are not written by this kernel).
+// The inverse factor is off the critical path of the factorisation, so its
+// products run on at most kInvCtas blocks (grid-stride over the work units):
+// fewer SMs then share their binary64 unit with the diagonal-tile kernel.
+constexpr int kInvCtas = 128;  // measured on the 1M torus: 64 leaves the inverse last, uncapped slows the diagonal tiles
 __global__ void __launch_bounds__(kQR * NB) k_trinv_update(double* __restrict__ X, const double* __restrict__ C,
-                                                           int64_t np, int i) {
+                                                           int64_t np, int i, int nunits) {
     __shared__ double l[kQR][NB + 1];
     __shared__ double xs[NB][NB + 1];
-    const int t = blockIdx.x / kQ, q0 = (blockIdx.x % kQ) * kQR;
-    const int k = i + 1 + t / (i + 1);
-    const int jb = t % (i + 1);
     const int rl = threadIdx.x / NB, c = threadIdx.x % NB;
-    l[rl][c] = C[((int64_t)k * NB + q0 + rl) * np + (int64_t)i * NB + c];
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int t = u / kQ, q0 = (u % kQ) * kQR;
+        const int k = i + 1 + t / (i + 1);
+        const int jb = t % (i + 1);
+        l[rl][c] = C[((int64_t)k * NB + q0 + rl) * np + (int64_t)i * NB + c];
 #pragma unroll
-    for (int q = 0; q < kQ; q++) xs[rl + kQR * q][c] = X[((int64_t)i * NB + rl + kQR * q) * np + (int64_t)jb * NB + c];
-    __syncthreads();
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int q = 0; q < kQ; q++)
+            xs[rl + kQR * q][c] = X[((int64_t)i * NB + rl + kQR * q) * np + (int64_t)jb * NB + c];
+        __syncthreads();
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int q = 0; q < NB; q++) s[q & 3] += l[rl][q] * xs[q][c];
-    X[((int64_t)k * NB + q0 + rl) * np + (int64_t)jb * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
+        for (int q = 0; q < NB; q++) s[q & 3] += l[rl][q] * xs[q][c];
+        X[((int64_t)k * NB + q0 + rl) * np + (int64_t)jb * NB + c] -= (s[0] + s[1]) + (s[2] + s[3]);
+        __syncthreads();  // the tiles in shared memory are reloaded for the next unit
+    }
 }
 
 __global__ void k_transpose(const double* __restrict__ X, double* __restrict__ XT, int64_t np) {
@@ -339,7 +347,10 @@ void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s) {
         }
         cudaStreamWaitEvent(s2, h->ev_step[j], 0);
         k_trinv_row<<<j + 1, NB * NB, 0, s2>>>(C.linv, np, j, C.dblk);
-        if (j + 1 < nb) k_trinv_update<<<(nb - j - 1) * (j + 1) * kQ, kQR * NB, 0, s2>>>(C.linv, C.chol, np, j);
+        if (j + 1 < nb) {
+            const int units = (nb - j - 1) * (j + 1) * kQ;
+            k_trinv_update<<<std::min(units, kInvCtas), kQR * NB, 0, s2>>>(C.linv, C.chol, np, j, units);
+        }
     }
     cudaEventRecord(h->ev_join, s2);
     cudaStreamWaitEvent(s, h->ev_join, 0);
