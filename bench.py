@@ -49,16 +49,23 @@ L2_FLUSH_BYTES = 256 << 20
 # only for the kernel source it was taken on; reported as null otherwise.
 TRAFFIC_CAPTURE = dict(bytes_per_sweep=28134144 + 28132352 + 28132864 + 28132864, bytes_per_launch=28.13e6,
                        source="paper_2104_13755_gb300/csrc/kernels.cuh",
-                       sha256="03ab622b827b9d3bf36ac2b60491a0c9726c6ea52ad714a7f83445c0c90f9673")
+                       region=("constexpr int kThreads = 256;", "// Damped Jacobi update"),
+                       sha256="09dc140ecb4867825f4cf277ac496b5156cdb6ea80da30788ba1a28eb9f53f18")
 
 
 def captured_traffic():
+    """The captured per-sweep traffic while the source of the measured kernel
+    (the sweep kernel and the helpers it uses, a fixed region of the header) is
+    the one that was captured; None once it has changed."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, TRAFFIC_CAPTURE["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != TRAFFIC_CAPTURE["sha256"]:
-                return None
-    except OSError:
+        with open(os.path.join(ROOT, TRAFFIC_CAPTURE["source"])) as f:
+            text = f.read()
+        first, last = TRAFFIC_CAPTURE["region"]
+        a, b = text.index(first), text.index(last)
+        if hashlib.sha256(text[a:b].encode()).hexdigest() != TRAFFIC_CAPTURE["sha256"]:
+            return None
+    except (OSError, ValueError):
         return None
     return TRAFFIC_CAPTURE["bytes_per_sweep"]
 

@@ -90,9 +90,9 @@ int lanes(const DLevel& L) {
 }
 
 template <typename T, int K>
-void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse, cudaStream_t s) {
+void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse, cudaStream_t s, int first = 0) {
     const int R = lanes<T>(L);
-    for (int cc = 0; cc < L.ncolours; cc++) {
+    for (int cc = first; cc < L.ncolours; cc++) {
         const int c = reverse ? L.ncolours - 1 - cc : cc;
         const int s0 = L.colour_slice[c], s1 = L.colour_slice[c + 1];
         if (s1 <= s0) continue;
@@ -111,9 +111,10 @@ void rec_residual(DLevel& L, const LevelView<T>& v, cudaStream_t s);
 // or damped Jacobi (r = b - A x into the level's residual buffer, then
 // x += omega D^{-1} r).
 template <typename T, int K>
-void rec_relax(const smg_hierarchy* h, DLevel& L, const LevelView<T>& v, bool reverse, cudaStream_t s) {
+void rec_relax(const smg_hierarchy* h, DLevel& L, const LevelView<T>& v, bool reverse, cudaStream_t s,
+               int first = 0) {
     if (h->opts.smoother != SMG_SMOOTHER_JACOBI) {
-        rec_sweep<T, K>(L, v, v.b, v.x, reverse, s);
+        rec_sweep<T, K>(L, v, v.b, v.x, reverse, s, first);
         return;
     }
     rec_residual<T, K>(L, v, s);
@@ -193,24 +194,33 @@ void rec_tail(smg_hierarchy* h, bool down, int t, cudaStream_t s) {
 }
 
 // One V-cycle of Alg. 2 on the level buffers (x_0, b_0 of the chosen precision).
-// Coarse levels start from x = 0: the restriction kernel writes that zero.
-// Levels [t, H) run in the cluster tail kernels.
+// Coarse levels start from x = 0, which the restriction kernel writes. On a
+// coarse level that the launched kernels relax with Gauss-Seidel, the first
+// pre-relaxation colour step from that zero is x_i = b_i / a_ii on colour
+// class 0 (bitwise, as the step computes it), so the restriction writes those
+// values and the step is not launched. Levels [t, H) run in the cluster tail
+// kernels.
 template <typename T, int K>
 void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
     const int H = h->H;
     const bool single = sizeof(T) == 4;
     const int t = tail_start(h, single, K);
+    const bool gs = h->opts.smoother != SMG_SMOOTHER_JACOBI && h->opts.mu_pre > 0;
+    auto seeded = [&](int l) { return gs && l >= 1 && l < t && h->L[l].seed_rows > 0; };
     for (int l = 0; l < t; l++) {
         DLevel& L = h->L[l];
         DLevel& N = h->L[l + 1];
         LevelView<T> v = view<T>(L);
         LevelView<T> vn = view<T>(N);
-        for (int it = 0; it < h->opts.mu_pre; it++) rec_relax<T, K>(h, L, v, false, s);  // pre-relaxation
+        for (int it = 0; it < h->opts.mu_pre; it++)  // pre-relaxation
+            rec_relax<T, K>(h, L, v, false, s, (it == 0 && seeded(l)) ? 1 : 0);
         rec_residual<T, K>(L, v, s);
         const dim3 grid(blocks_for(N.n * 4)), block(kern::kThreads);
         const T* r = v.r;
+        const T* dinv_n = vn.dinv;
+        const int nseed = seeded(l + 1) ? N.seed_rows : 0;
         ck(launch_pdl(kern::restrict_rows<T, K>, grid, block, s, (int)N.n, L.pt_ptr, L.pt_row, v.pt_w, r, vn.b,
-                      vn.x), "restrict launch");
+                      vn.x, dinv_n, nseed), "restrict launch");
     }
     if (t < H) rec_tail<T, K>(h, true, t, s);
     DLevel& C = h->L[H];
@@ -959,6 +969,7 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
         L.sell_col = upload(h, lp.sell_col);
         L.colour_slice_dev = upload(h, lp.colour_slice);
         L.colour_row_dev = upload(h, lp.colour_row);
+        L.seed_rows = (lp.colour_row.size() > 1 && lp.colour_row[0] == 0) ? lp.colour_row[1] : 0;
         for (const SliceMeta& m : lp.slices) L.maxw = std::max(L.maxw, (int)m.width);
         L.dinv = dalloc<double>(h, L.n);
         L.vals32 = dalloc<float>(h, L.nflat);

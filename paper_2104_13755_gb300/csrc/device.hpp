@@ -37,6 +37,7 @@ struct DLevel {
     int32_t* colour_row_dev = nullptr;
     int maxw = 0;  // widest slice (off-diagonal entries per row)
     std::vector<int32_t> colour_slice;  // host copy, ncolours + 1
+    int32_t seed_rows = 0;              // rows of colour class 0 when they are rows [0, seed_rows), else 0
     // cluster tail: per-CTA work-unit tables (see TailLevel), binary64 and binary32
     struct TailTable {
         int32_t* tab = nullptr;

@@ -211,13 +211,17 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) residual(con
 }
 
 // Restriction r_{h+1} = P^T r_h (Alg. 2 "restrict residual") through the CSR of
-// P^T, four lanes per coarse row, plus the zero start x_{h+1} = 0 of the coarse
-// cycle (the coarse iterate is not read again before its pre-relaxation).
+// P^T, four lanes per coarse row, plus the start of the coarse cycle's iterate.
+// That start is x_{h+1} = 0, and the first Gauss-Seidel colour step from it
+// gives each row of colour class 0 (rows [0, nseed)) exactly b_i / a_ii (its
+// neighbours are all zero, and fma(-a, 0, b) = b), so with nseed > 0 this
+// kernel writes that value and the caller skips that colour step.
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) restrict_rows(int nc, const int32_t* __restrict__ ptr,
                                                           const int32_t* __restrict__ rows, const T* __restrict__ w,
                                                           const T* __restrict__ r, T* __restrict__ bc,
-                                                          T* __restrict__ xc) {
+                                                          T* __restrict__ xc, const T* __restrict__ dinv_c,
+                                                          int nseed) {
     constexpr int RR = 4, PREP = 4;
     const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) / RR);
     const int sub = threadIdx.x % RR;
@@ -231,6 +235,7 @@ __global__ void __launch_bounds__(kThreads) restrict_rows(int nc, const int32_t*
         ri[u] = k < k1 ? rows[k] : 0;
         wi[u] = k < k1 ? w[k] : T(0);
     }
+    const T dseed = I < nseed ? dinv_c[I] : T(0);
     pdl_wait();
     pdl_trigger();
     T acc[K];
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) restrict_rows(int nc, const int32_t*
 #pragma unroll
         for (int q = 0; q < K; q++) {
             bc[(int64_t)I * K + q] = acc[q];
-            xc[(int64_t)I * K + q] = T(0);
+            xc[(int64_t)I * K + q] = I < nseed ? acc[q] * dseed : T(0);
         }
 }
 
