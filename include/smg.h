@@ -232,6 +232,10 @@ int  smg_update_matrix(smg_hierarchy *h, const double *vals_dev, smg_stream stre
  * the call then synchronises `stream` to fill `info` (may be NULL).
  * Returns SMG_OK when converged, SMG_ERR_NOT_CONVERGED / SMG_ERR_DIVERGED
  * otherwise (x_dev then holds the last iterate).  nrhs in 1..4.
+ * SMG_ERR_NOT_SPD: the last update's coarsest factor met a pivot that is not
+ * positive.  SMG_ERR_TIMEOUT: a bounded wait of the cluster-tail kernels gave
+ * up (a step's values never arrived); the result is not valid and the
+ * hierarchy keeps reporting it until destroyed.
  */
 int  smg_solve(smg_hierarchy *h, const double *b_dev, double *x_dev, int nrhs, smg_info *info,
                smg_stream stream);

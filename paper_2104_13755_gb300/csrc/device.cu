@@ -1285,7 +1285,7 @@ int smg_solve_result(smg_hierarchy* h, smg_info* info) {
         info->rho = (ss.cycles > 0 && ss.rel0 > 0) ? std::pow(ss.rel / ss.rel0, 1.0 / ss.cycles) : 0.0;
     }
     if (ss.chol_bad) return fail("coarsest operator is not positive definite", SMG_ERR_NOT_SPD);
-    if (ss.tail_err) return fail("cluster tail: wait for staged matrix entries timed out", SMG_ERR_CUDA);
+    if (ss.tail_err) return fail("cluster tail: a step barrier wait timed out", SMG_ERR_TIMEOUT);
     if (ss.status == SMG_ERR_NOT_CONVERGED) return fail("not converged within max_cycles", ss.status);
     if (ss.status == SMG_ERR_DIVERGED) return fail("residual became non-finite", ss.status);
     return SMG_OK;
