@@ -233,7 +233,7 @@ class Decimator {
     std::vector<double> u_, best_u_, work_;
     std::vector<int32_t> nb_, occ_, opp_, ni_, nj_, common_, moving_;
     std::vector<int> fixed_;
-    std::vector<double> fixval_, angsum_, before_sum_, muv_;
+    std::vector<double> fixval_, angsum_, before_sum_, muv_, fuv_;
     std::vector<std::pair<int32_t, int>> bv_;
     // rejected edges, listed at both endpoints; re-queued when a neighbourhood changes
     std::vector<std::vector<int32_t>> rej_;
@@ -627,15 +627,26 @@ bool Decimator::try_collapse(int32_t i, int32_t j) {
     pos_[3 * i + 2] = pk.z;
     alive_count_--;
 
+    // UV corners and doubled area of every new face, once per collapse
+    std::vector<double>& fuv = fuv_;
+    fuv.resize(7 * Fa_.size());
+    for (size_t a = 0; a < Fa_.size(); a++) {
+        const int32_t f = Fa_[a];
+        int t0 = var_after(fv_[3 * f]), t1 = var_after(fv_[3 * f + 1]), t2 = var_after(fv_[3 * f + 2]);
+        double* g = &fuv[7 * a];
+        g[0] = U[2 * t0]; g[1] = U[2 * t0 + 1]; g[2] = U[2 * t1]; g[3] = U[2 * t1 + 1];
+        g[4] = U[2 * t2]; g[5] = U[2 * t2 + 1];
+        g[6] = cross2(g[2] - g[0], g[3] - g[1], g[4] - g[0], g[5] - g[1]);
+    }
     for (size_t q = 0; q < moving.size(); q++) {
         double x = muv[2 * q], y = muv[2 * q + 1];
         int32_t best_f = -1;
         double best_min = -1e300, bb[3] = {0, 0, 0};
-        for (int32_t f : Fa_) {
-            int t0 = var_after(fv_[3 * f]), t1 = var_after(fv_[3 * f + 1]), t2 = var_after(fv_[3 * f + 2]);
-            double x0 = U[2 * t0], y0 = U[2 * t0 + 1], x1 = U[2 * t1], y1 = U[2 * t1 + 1];
-            double x2 = U[2 * t2], y2 = U[2 * t2 + 1];
-            double dbl = cross2(x1 - x0, y1 - y0, x2 - x0, y2 - y0);
+        for (size_t a = 0; a < Fa_.size(); a++) {
+            const int32_t f = Fa_[a];
+            const double* g = &fuv[7 * a];
+            double x0 = g[0], y0 = g[1], x1 = g[2], y1 = g[3], x2 = g[4], y2 = g[5];
+            double dbl = g[6];
             double b0 = cross2(x1 - x, y1 - y, x2 - x, y2 - y) / dbl;
             double b1 = cross2(x2 - x, y2 - y, x0 - x, y0 - y) / dbl;
             double b2 = cross2(x0 - x, y0 - y, x1 - x, y1 - y) / dbl;
