@@ -145,6 +145,20 @@ def test_plan_save_load_roundtrip(tmp_path, disk_plan):
     assert e.value.status == 11
 
 
+def test_plan_is_bitwise_deterministic(tmp_path):
+    """Setup is deterministic: two builds of the same mesh save identical
+    bytes.  The mesh is large enough (> 4096 rows at level 0) that the
+    Galerkin and transfer plans are built on several host threads."""
+    V, F = synth.perturbed_icosphere(5, seed=2)
+    blobs = []
+    for k in range(2):
+        path = str(tmp_path / ("p%d.smgplan" % k))
+        smg.Plan(V, F).save(path)
+        with open(path, "rb") as f:
+            blobs.append(f.read())
+    assert len(blobs[0]) > 0 and blobs[0] == blobs[1]
+
+
 @pytest.mark.parametrize("dirichlet", [False, True])
 def test_two_ring_plan_patterns_and_colouring_match_oracle(dirichlet):
     """pattern_rings = 2 (Sec. 6: Bilaplacian-type systems): the level-0 pattern
