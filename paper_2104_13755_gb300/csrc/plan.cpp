@@ -580,21 +580,21 @@ int finalize_plan(Plan& p, std::string& err) {
         }
     }
     {
-        // edge -> corners opposite to it
-        std::vector<std::pair<int64_t, int32_t>> eo;
-        eo.reserve(3 * A.nf);
-        for (int64_t f = 0; f < A.nf; f++)
-            for (int c = 0; c < 3; c++) {
-                int64_t a = A.F[3 * f + (c + 1) % 3], b = A.F[3 * f + (c + 2) % 3];
-                eo.push_back({std::min(a, b) * n0 + std::max(a, b), (int32_t)(3 * f + c)});
-            }
-        std::sort(eo.begin(), eo.end());
+        // corners opposite edge (a, b): the two smallest corner codes 3f + c over
+        // the faces f around a that also hold b, c the corner that is neither
         auto opp_of = [&](int64_t a, int64_t b, int32_t& o0, int32_t& o1) {
-            int64_t key = std::min(a, b) * n0 + std::max(a, b);
-            auto it = std::lower_bound(eo.begin(), eo.end(), std::make_pair(key, (int32_t)-1));
             o0 = o1 = -1;
-            if (it != eo.end() && it->first == key) { o0 = it->second; ++it; }
-            if (it != eo.end() && it->first == key) { o1 = it->second; }
+            for (int32_t q = A.vinc_ptr[a]; q < A.vinc_ptr[a + 1]; q++) {
+                const int32_t code = A.vinc_code[q];
+                const int64_t f = code / 3;
+                const int ca = code % 3;
+                for (int c = 0; c < 3; c++) {
+                    if (c == ca || A.F[3 * f + c] != b) continue;
+                    const int32_t o = (int32_t)(3 * f + (3 - ca - c));
+                    if (o0 < 0 || o < o0) { o1 = o0; o0 = o; }
+                    else if (o1 < 0 || o < o1) { o1 = o; }
+                }
+            }
         };
         A.opp0.assign(l0.nflat, -1);
         A.opp1.assign(l0.nflat, -1);
