@@ -177,7 +177,29 @@ struct Flattening {
             if (!(dj > 1e-300)) return false;
             double ljj = std::sqrt(dj);
             K[(size_t)j * f + j] = ljj;
-            for (int i = j + 1; i < f; i++) {
+            const double* Kj = K + (size_t)j * f;
+            int i = j + 1;
+            // four rows' sums side by side: each keeps its own order of
+            // operations, so the factor is bitwise the one-row-at-a-time one
+            for (; i + 3 < f; i += 4) {
+                double* K0 = K + (size_t)i * f;
+                double* K1 = K0 + f;
+                double* K2 = K1 + f;
+                double* K3 = K2 + f;
+                double s0 = K0[j], s1 = K1[j], s2 = K2[j], s3 = K3[j];
+                for (int k = 0; k < j; k++) {
+                    const double jk = Kj[k];
+                    s0 -= K0[k] * jk;
+                    s1 -= K1[k] * jk;
+                    s2 -= K2[k] * jk;
+                    s3 -= K3[k] * jk;
+                }
+                K0[j] = s0 / ljj;
+                K1[j] = s1 / ljj;
+                K2[j] = s2 / ljj;
+                K3[j] = s3 / ljj;
+            }
+            for (; i < f; i++) {
                 double s = K[(size_t)i * f + j];
                 for (int k = 0; k < j; k++) s -= K[(size_t)i * f + k] * K[(size_t)j * f + k];
                 K[(size_t)i * f + j] = s / ljj;
