@@ -98,6 +98,29 @@ def test_pcg_mixed_precision(torus):
     assert abs(info["cycles"] - ref.cycles) <= 1
 
 
+@pytest.mark.parametrize("name", ["torus", "disk"])
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_pcg_mixed_iterates_match_oracle(name, nrhs, request):
+    """CG with the binary32 cycle as preconditioner: the GPU and the oracle
+    compute z = B32 r with binary32 cycles that differ only in summation
+    order (a few units of 2^-24 relative); CG's binary64 recurrences carry
+    that difference on with modest growth over the first iterations, so the
+    iterates are held to 5e-6 (~80 u) relative, entry by entry against the
+    largest (measured on GB300: at most 2.7e-7 after one iteration, less
+    after more)."""
+    c = request.getfixturevalue(name)
+    b = synth.uniform_rhs(c.n, nrhs=nrhs, seed=24)
+    bd = to_dev(b)
+    for k in (1, 2, 4):
+        c.h.set_options(rtol=1e-30, max_cycles=k, solver=smg.PCG, precision=smg.MIXED)
+        x, info = c.h.solve(bd, check=False)
+        assert info["cycles"] == k
+        ref = oracle.pcg(c.levels, b, opt=oracle.Options(rtol=1e-30, max_cycles=k), single=True)
+        xg = x.cpu().numpy()
+        assert np.abs(xg - ref.x).max() <= 5e-6 * np.abs(ref.x).max(), k
+    c.h.set_options(rtol=1e-10, solver=smg.VCYCLE, precision=smg.FP64)
+
+
 def test_pcg_single_level_is_one_step():
     V, F = synth.perturbed_icosphere(2, seed=1)
     c = Case(V, F, 1e-2, max_levels=1)

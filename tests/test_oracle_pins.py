@@ -177,6 +177,40 @@ def test_gauss_seidel_equals_matrix_splitting():
         assert np.abs(x32[order] - xp).max() < 1e-5 * np.abs(xp).max()
 
 
+def test_single_precision_sweep_within_rounding_error_bound():
+    """The binary32 sweep is a triangular solve carried out in binary32:
+    row i computes x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii with the newest
+    x_j (earlier rows of the order) and the old x_j (later rows).  With the
+    binary32 inputs taken exactly, the textbook rounding analysis of a sum of
+    m products followed by a division (Higham, "Accuracy and Stability of
+    Numerical Algorithms", Lemma 3.1 and Sec. 8.1) bounds the residual of
+    every row componentwise by gamma_{m+2} times the sum of the magnitudes
+    of its terms, gamma_k = k u / (1 - k u) with u = 2^-24.  The computed
+    values are binary32 numbers, and they are not the binary64 sweep of the
+    same inputs (which would leave a residual near 2^-53)."""
+    V, F = synth.perturbed_icosphere(2, seed=8)
+    A = oracle.system_matrix(V, F, 1e-2).astype(np.float32)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal((A.shape[0], 2)).astype(np.float32)
+    x0 = rng.standard_normal((A.shape[0], 2)).astype(np.float32)
+    col = oracle.greedy_colouring(A)
+    u = 2.0 ** -24
+    for reverse in (False, True):
+        order = oracle.colour_order(col, reverse)
+        x = x0.copy()
+        oracle.gs_sweep(A, x, b, order)
+        assert x.dtype == np.float32
+        Ap = A.toarray().astype(np.float64)[np.ix_(order, order)]
+        lo, up = np.tril(Ap), np.triu(Ap, 1)
+        xn, xo, bp = x[order].astype(np.float64), x0[order].astype(np.float64), b[order].astype(np.float64)
+        res = lo @ xn - (bp - up @ xo)
+        mag = np.abs(lo) @ np.abs(xn) + np.abs(up) @ np.abs(xo) + np.abs(bp)
+        m = np.diff(A.indptr)[order][:, None] - 1
+        gamma = (m + 2) * u / (1 - (m + 2) * u)
+        assert np.all(np.abs(res) <= gamma * mag)
+        assert np.max(np.abs(res) / mag) > 1e-3 * u
+
+
 def test_cholesky_against_lapack_and_not_spd():
     rng = np.random.default_rng(3)
     B = rng.standard_normal((30, 30))
@@ -250,6 +284,82 @@ def test_mixed_precision_reaches_direct_solution(torus_pin_hierarchy):
     xs = spla.splu(A.tocsc()).solve(b)
     assert res.history[-1] <= 1e-10
     assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) < 1e-9
+
+
+def _binary32_exact_levels(A0, Ps):
+    """A hierarchy whose operators are all binary32 numbers: every level's
+    matrix is the binary32 rounding of the Galerkin product of the level
+    above (the prolongations used here hold 1 and 1/2, exact in binary32), so
+    the binary32 copies equal the binary64 operators and a binary32 cycle
+    differs from a binary64 cycle by arithmetic alone."""
+    r32 = lambda M: M.astype(np.float32).astype(np.float64).tocsr()
+    A = r32(A0)
+    levels = []
+    for P in Ps:
+        assert np.array_equal(P.data.astype(np.float32).astype(np.float64), P.data)
+        col = oracle.greedy_colouring(A)
+        levels.append(oracle.Level(A=A, P=P.tocsr(), colour=col, fwd=oracle.colour_order(col),
+                                   rev=oracle.colour_order(col, reverse=True)))
+        A = r32(oracle.galerkin(A, P))
+    levels.append(oracle.Level(A=A, L=oracle.cholesky(A.toarray())))
+    for lv in levels:
+        lv.A32 = lv.A.astype(np.float32)
+        lv.P32 = None if lv.P is None else lv.P.astype(np.float32)
+    return levels
+
+
+def test_single_precision_cycle_is_binary32_arithmetic(torus_pin_hierarchy):
+    """One cycle with single=True returns binary32 values, and on operators
+    and a right-hand side that are exact binary32 numbers it differs from the
+    binary64 cycle by arithmetic rounding alone: more than 1e-9 relative
+    (binary64 arithmetic anywhere in place of binary32, e.g. a binary64
+    operator mixed into the sweep, would agree to ~1e-15) and less than 1e-5
+    (a few hundred units of u = 2^-24; a wrong operator or a dropped term is
+    O(1)); and most entries differ from the binary32 rounding of the binary64
+    result, which a binary64 cycle rounded only at its end would reproduce."""
+    V, F, Ps = torus_pin_hierarchy
+    A = oracle.system_matrix(V, F, 1e-3)
+    levels = _binary32_exact_levels(A, Ps)
+    for nrhs in (1, 3):
+        b32 = synth.uniform_rhs(A.shape[0], nrhs=nrhs, seed=9).astype(np.float32)
+        d32 = oracle.vcycle(levels, 0, np.zeros_like(b32), b32, oracle.Options(), single=True)
+        assert d32.dtype == np.float32
+        b64 = b32.astype(np.float64)
+        d64 = oracle.vcycle(levels, 0, np.zeros_like(b64), b64, oracle.Options())
+        diff = np.linalg.norm(d32 - d64) / np.linalg.norm(d64)
+        assert 1e-9 < diff < 1e-5, diff
+        # binary32 rounding of every operation, not only of the result: a
+        # binary64 cycle rounded once at the end would equal round32(d64)
+        assert np.mean(d32 != d64.astype(np.float32)) > 0.1
+
+
+def test_mixed_refinement_tracks_binary64_cycles(torus_pin_hierarchy):
+    """A V-cycle is an affine map x -> x + B (b - A x) (every Gauss-Seidel
+    sweep, the coarse correction and the direct solve are linear in x and
+    b, with A^-1 b as fixed point), and a cycle from zero on the residual
+    r = b - A x returns B r.  So refinement step k of the mixed form,
+    x_k = x_{k-1} + B32 (b - A x_{k-1}), equals binary64 cycle k of Alg. 1
+    except for binary32 rounding in B32: the two iterates differ by a small
+    multiple of u = 2^-24 times the size of that step's correction (the
+    earlier differences are contracted by the cycle), and by more than
+    binary64 rounding at the first step."""
+    V, F, Ps = torus_pin_hierarchy
+    A = oracle.system_matrix(V, F, 1e-3)
+    levels = oracle.build_levels(A, Ps)
+    for nrhs in (1, 2):
+        b = synth.uniform_rhs(A.shape[0], nrhs=nrhs, seed=10)
+        opt = oracle.Options(rtol=1e-12)
+        mx = oracle.solve_mixed(levels, b, opt=opt, keep_iterates=True)
+        fp = oracle.solve(levels, b, opt=opt, keep_iterates=True)
+        assert mx.cycles >= 3 and fp.cycles >= 3
+        prev = np.zeros_like(b)
+        for k in range(min(mx.cycles, fp.cycles)):
+            step = np.abs(fp.iterates[k] - prev).max()
+            gap = np.abs(mx.iterates[k] - fp.iterates[k]).max()
+            assert gap <= 1e-5 * step + 1e-14 * np.abs(fp.iterates[k]).max(), k
+            if k == 0:
+                assert gap > 1e-9 * step
+            prev = fp.iterates[k]
 
 
 def test_dirichlet_reduction_solves_constrained_minimum():
