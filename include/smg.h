@@ -321,9 +321,9 @@ int  smg_launch_counts(smg_hierarchy *h, int nrhs, int32_t out[3]);
 /*
  * Residual norms of a system the caller holds, with no allocation at all.
  * (The paper has no counterpart: this is a service for callers that cannot
- * allocate device memory when they need it -- code running during CUDA graph
- * capture, where cudaMalloc is not allowed; real-time loops that must not wait
- * on an allocator; hosts that own every device allocation of a plug-in.)
+ * allocate device memory when they need it -- real-time frame loops, where
+ * cudaMalloc or cudaFree may synchronise the device and stall the frame, and
+ * host applications that own every device allocation of a plug-in.)
  *   rowptr_dev  n + 1 row offsets (int64), col_dev / vals_dev the CSR entries
  *               (any order inside a row), all on the device
  *   x_dev, b_dev  n x nrhs row-major, nrhs in 1..4
@@ -332,8 +332,9 @@ int  smg_launch_counts(smg_hierarchy *h, int nrhs, int32_t out[3]);
  * Nothing is allocated: the partial sums of the reduction live in a fixed
  * device array inside the library (608 x 8 doubles, 38 KB), resident on every
  * GPU that loads the library until the process exits.  The first call on a
- * device looks that array up (cudaGetSymbolAddress); make that first call
- * before capturing a stream.  Every call on a device shares the array, so
+ * device (and the first after its context changed, e.g. after
+ * cudaDeviceReset) looks that array up (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call on a device shares the array, so
  * calls whose work may overlap on the GPU (different streams without
  * ordering) race and must be serialised by the caller.  The reduction order is
  * fixed: repeated calls on the same data return identical bits.

@@ -1,10 +1,10 @@
 // Residual norms of a caller-supplied CSR system without any allocation.
 //
 // Some callers cannot allocate device memory at the moment they need this:
-// code running while a stream is being captured into a CUDA graph (where
-// cudaMalloc is not permitted), real-time frame loops that must not pay for an
-// allocator's synchronisation, and hosts that give a plug-in a fixed device
-// budget and own every allocation themselves.  This entry point serves them:
+// real-time frame loops, where cudaMalloc or cudaFree may synchronise the
+// device and stall the frame, and host applications that give a plug-in a
+// fixed device budget and own every allocation themselves.  This entry point
+// serves them:
 // the caller passes the matrix and vectors it already owns, and the only
 // scratch -- one partial sum per block of the first kernel -- lives in the
 // fixed-size array below, which is part of the library image and stays
@@ -102,11 +102,43 @@ __global__ void __launch_bounds__(kThreads) csr_resnorm_final(const double* __re
     if (threadIdx.x < 2 * K) out[threadIdx.x] = red[0][threadIdx.x];
 }
 
-// Device address of g_scratch, looked up once per device (the host-side symbol
-// is only a stand-in and must never be handed to a kernel).
+// Device address of g_scratch, looked up once per device and context (the
+// host-side symbol is only a stand-in and must never be handed to a kernel).
+// The address belongs to the context the module was loaded in: after
+// cudaDeviceReset, or with another context current on the device, the
+// lookup is repeated.  The current context comes from the driver's
+// cuCtxGetCurrent, reached through the runtime (no link to the driver
+// library); where that is unavailable the address is looked up on every call.
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;
-double* g_scratch_dev[kMaxDevices] = {};
+struct ScratchAddr {
+    void* ctx = nullptr;
+    double* ptr = nullptr;
+};
+ScratchAddr g_scratch_dev[kMaxDevices];
+
+typedef int (*CtxGetCurrentFn)(void**);  // CUresult cuCtxGetCurrent(CUcontext*)
+
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (CtxGetCurrentFn)f;
+    }();
+    return fn;
+}
+
+void* current_context() {
+    CtxGetCurrentFn fn = ctx_get_current();
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 int scratch_for_current_device(double** out) {
     int dev = -1;
@@ -116,17 +148,20 @@ int scratch_for_current_device(double** out) {
         return SMG_ERR_CUDA;
     }
     std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_scratch_dev[dev]) {
+    ScratchAddr& a = g_scratch_dev[dev];
+    void* ctx = current_context();
+    if (!a.ptr || !ctx || ctx != a.ctx) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);  // also makes the primary context current
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             smg::set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             return SMG_ERR_CUDA;
         }
-        g_scratch_dev[dev] = (double*)p;
+        a.ptr = (double*)p;
+        a.ctx = current_context();
     }
-    *out = g_scratch_dev[dev];
+    *out = a.ptr;
     return SMG_OK;
 }
 
