@@ -305,6 +305,14 @@ int  smg_run_stage(smg_hierarchy *h, int stage, int level, int nrhs, int precisi
  * kernels, out[1] of the binary32 kernels, out[2] colour classes, out[3] slices. */
 int  smg_level_config(const smg_hierarchy *h, int level, int32_t out[4]);
 
+/* Residual fused with restriction from level l to l + 1 (Alg. 2 "compute
+ * residual", "restrict residual" as one product b_{l+1} = P^T b_l - Q x_l with
+ * Q = P^T A_l, the first stage of the Galerkin product of Eq. gca): out[0]
+ * entries of Q, out[1] entries of P^T, out[2] padded slots of the operator's
+ * SELL-32 layout, out[3] / out[4] lanes per row of its binary64 / binary32
+ * kernel.  level in 0..H-1. */
+int  smg_level_restriction(const smg_hierarchy *h, int level, int64_t out[5]);
+
 /* Cycle configuration: out[0] = H, out[1] / out[2] = first level whose
  * smoothing and transfers run inside one thread-block cluster launch per
  * half-cycle for binary64 / binary32 cycles (H = none), out[3] = CTAs per

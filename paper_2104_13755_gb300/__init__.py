@@ -90,6 +90,7 @@ def _load():
         "smg_level_matrix": (I32, [P, I32, P, P]),
         "smg_run_stage": (I32, [P, I32, I32, I32, I32, I32, P]),
         "smg_level_config": (I32, [P, I32, P]),
+        "smg_level_restriction": (I32, [P, I32, P]),
         "smg_cycle_config": (I32, [P, P]),
         "smg_device_bytes": (I64, [P]),
         "smg_residual_norms_noalloc": (I32, [I64, P, P, P, P, P, I32, P, P]),
@@ -391,6 +392,13 @@ class Hierarchy:
         """(lanes per row binary64, lanes per row binary32, colours, slices) of a level."""
         out = (ctypes.c_int32 * 4)()
         _check(lib.smg_level_config(self._h, level, out), "smg_level_config")
+        return tuple(out)
+
+    def level_restriction(self, level):
+        """(entries of Q = P^T A_l, entries of P^T, padded slots, lanes per row binary64,
+        binary32) of the fused residual-restriction operator from `level` to the next."""
+        out = (ctypes.c_int64 * 5)()
+        _check(lib.smg_level_restriction(self._h, level, out), "smg_level_restriction")
         return tuple(out)
 
     def cycle_config(self):

@@ -57,7 +57,7 @@ void drop_graphs(smg_hierarchy* h);
 // ------------------------------------------------------------------ launchers
 template <typename T>
 struct LevelView {
-    const T *sval, *diag, *dinv, *p_w, *pt_w;
+    const T *sval, *diag, *dinv, *p_w, *pt_w, *rq;
     T *x, *b, *r;
 };
 
@@ -65,11 +65,11 @@ template <typename T>
 LevelView<T> view(DLevel& L);
 template <>
 LevelView<double> view<double>(DLevel& L) {
-    return {L.vals + L.sbase, L.vals, L.dinv, L.p_w, L.pt_w, L.x, L.b, L.r};
+    return {L.vals + L.sbase, L.vals, L.dinv, L.p_w, L.pt_w, L.rq_val, L.x, L.b, L.r};
 }
 template <>
 LevelView<float> view<float>(DLevel& L) {
-    return {L.vals32 + L.sbase, L.vals32, L.dinv32, L.p_w32, L.pt_w32, L.x32, L.b32, L.r32};
+    return {L.vals32 + L.sbase, L.vals32, L.dinv32, L.p_w32, L.pt_w32, L.rq_val32, L.x32, L.b32, L.r32};
 }
 
 // Dispatch on the lanes-per-row of a level (compile-time RR inside CALL).
@@ -136,6 +136,27 @@ void rec_residual(DLevel& L, const LevelView<T>& v, cudaStream_t s) {
     const T* x = v.x;
     SMG_R_SWITCH(R, ck(launch_pdl(kern::residual<T, K, RR>, grid, block, s, sl, L.nslices, col, v.sval, v.diag, b,
                                     x, v.r), "residual launch"));
+}
+
+template <typename T>
+int rq_lanes(const DLevel& L) {
+    return sizeof(T) == 4 ? L.Rq32 : L.Rq;
+}
+
+// Residual fused with restriction from level l into level l + 1 (one launch).
+template <typename T, int K>
+void rec_restrict_fused(DLevel& L, const LevelView<T>& v, const LevelView<T>& vn, int nseed, cudaStream_t s) {
+    const int R = rq_lanes<T>(L);
+    const dim3 grid(blocks_for((int64_t)L.rq_nslices * 32 * R)), block(kern::kThreads);
+    const RQSlice* sl = L.rq_slices;
+    const int32_t* row = L.rq_row;
+    const int32_t* col = L.rq_col;
+    const T* val = v.rq;
+    const T* b = v.b;
+    const T* x = v.x;
+    const T* dinv_n = vn.dinv;
+    SMG_R_SWITCH(R, ck(launch_pdl(kern::restrict_fused<T, K, RR>, grid, block, s, sl, L.rq_nslices, row, col, val, b,
+                                    x, vn.b, vn.x, dinv_n, nseed), "fused restriction launch"));
 }
 
 // Shared-memory slots of the cluster tail: per level, the replica of x (n
@@ -214,13 +235,8 @@ void rec_vcycle(smg_hierarchy* h, cudaStream_t s) {
         LevelView<T> vn = view<T>(N);
         for (int it = 0; it < h->opts.mu_pre; it++)  // pre-relaxation
             rec_relax<T, K>(h, L, v, false, s, (it == 0 && seeded(l)) ? 1 : 0);
-        rec_residual<T, K>(L, v, s);
-        const dim3 grid(blocks_for(N.n * 4)), block(kern::kThreads);
-        const T* r = v.r;
-        const T* dinv_n = vn.dinv;
         const int nseed = seeded(l + 1) ? N.seed_rows : 0;
-        ck(launch_pdl(kern::restrict_rows<T, K>, grid, block, s, (int)N.n, L.pt_ptr, L.pt_row, v.pt_w, r, vn.b,
-                      vn.x, dinv_n, nseed), "restrict launch");
+        rec_restrict_fused<T, K>(L, v, vn, nseed, s);  // b_{l+1} = P^T (b_l - A_l x_l), x_{l+1} = start
     }
     if (t < H) rec_tail<T, K>(h, true, t, s);
     DLevel& C = h->L[H];
@@ -546,6 +562,40 @@ void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
             if (prec == 0) L.R = bestR;
             else L.R32 = bestR;
         }
+        // lanes per row of the fused residual-restriction kernel, the same way
+        DLevel& N = h->L[l + 1];
+        for (int prec = 0; prec < 2; prec++) {
+            float best = 1e30f;
+            int bestR = prec == 0 ? L.Rq : L.Rq32;
+            for (int cand : {2, 4, 8, 16}) {
+                if (prec == 0) L.Rq = cand;
+                else L.Rq32 = cand;
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; rep++) {
+                    auto run = [&] {
+                        if (prec == 0) rec_restrict_fused<double, 1>(L, view<double>(L), view<double>(N), 0, h->cap);
+                        else rec_restrict_fused<float, 1>(L, view<float>(L), view<float>(N), 0, h->cap);
+                    };
+                    run();
+                    ck(cudaEventRecord(e0, h->cap), "event");
+                    for (int it = 0; it < 4; it++) run();
+                    ck(cudaEventRecord(e1, h->cap), "event");
+                    ck(cudaEventSynchronize(e1), "event sync");
+                    float t = 0.f;
+                    ck(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+                    ms = rep == 0 ? t : std::min(ms, t);
+                }
+                if (std::getenv("SMG_TRACE_TUNE"))
+                    std::fprintf(stderr, "[smg tune] level %d %s fused restriction, %2d lanes/row: %.1f us\n", l,
+                                 prec ? "f32" : "f64", cand, ms * 250.0f);
+                if (ms < best * 0.97f) {
+                    best = ms;
+                    bestR = cand;
+                }
+            }
+            if (prec == 0) L.Rq = bestR;
+            else L.Rq32 = bestR;
+        }
     }
     if (tune) {
         cudaEventDestroy(e0);
@@ -801,19 +851,32 @@ void choose_tail(smg_hierarchy* h, bool tune) {
     cudaEventDestroy(e1);
 }
 
-// Galerkin chain, level preparation and the coarsest factor.
-void rec_update(smg_hierarchy* h, cudaStream_t s) {
-    ck(cudaMemsetAsync(&h->state->chol_bad, 0, sizeof(int32_t), s), "memset");
-    for (int l = 0; l < h->H; l++) {
-        DLevel& L = h->L[l];
-        DLevel& N = h->L[l + 1];
-        kern::galerkin<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_w, L.vals, N.vals);
-    }
+// Galerkin stage 1 (Q = P^T A_l from the flat values `fine` into `rq`) and,
+// with `coarse`, stage 2 (A_{l+1} = Q P).
+void rec_galerkin(DLevel& L, DLevel& N, const double* fine, double* rq, double* coarse, cudaStream_t s) {
+    kern::galerkin_q<<<blocks_for(L.rq_nq), kern::kThreads, 0, s>>>(L.rq_nq, L.q_dst, L.q_ptr, L.q_src, L.q_pw, fine,
+                                                                    L.p_w, rq);
+    if (coarse)
+        kern::galerkin_qp<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_pw, rq, L.p_w,
+                                                                         coarse);
+}
+
+// Reciprocal diagonals and binary32 copies of every level (operators and fused
+// restriction operators).
+void rec_prep_levels(smg_hierarchy* h, cudaStream_t s) {
     for (int l = 0; l < h->H; l++) {
         DLevel& L = h->L[l];
         kern::prep_level<<<blocks_for(L.nflat), kern::kThreads, 0, s>>>(L.nflat, L.n, L.vals, L.dinv, L.vals32,
                                                                       L.dinv32);
+        kern::copy_f32<<<blocks_for(L.rq_nslots), kern::kThreads, 0, s>>>(L.rq_nslots, L.rq_val, L.rq_val32);
     }
+}
+
+// Galerkin chain, level preparation and the coarsest factor.
+void rec_update(smg_hierarchy* h, cudaStream_t s) {
+    ck(cudaMemsetAsync(&h->state->chol_bad, 0, sizeof(int32_t), s), "memset");
+    for (int l = 0; l < h->H; l++) rec_galerkin(h->L[l], h->L[l + 1], h->L[l].vals, h->L[l].rq_val, h->L[l + 1].vals, s);
+    rec_prep_levels(h, s);
     record_coarsest_factor(h, s);
 }
 
@@ -835,8 +898,16 @@ void ensure_split(smg_hierarchy* h, cudaStream_t s) {
     for (int l = 0; l < h->H; l++) {
         DLevel& L = h->L[l];
         DLevel& N = h->L[l + 1];
-        kern::galerkin<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_w, L.Lg, N.Lg);
-        kern::galerkin<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_w, L.Mg, N.Mg);
+        if (!L.rq_L) {  // P^T L and P^T M in the fused restriction layout; the restriction
+                        // segment of rq_M keeps -P^T (as rq_val does), rq_L holds 0 there,
+                        // so rq_val = rq_M + t rq_L slot by slot
+            L.rq_L = dalloc<double>(h, L.rq_nslots);
+            L.rq_M = dalloc<double>(h, L.rq_nslots);
+            ck(cudaMemsetAsync(L.rq_L, 0, sizeof(double) * L.rq_nslots, s), "memset");
+            ck(cudaMemcpyAsync(L.rq_M, L.rq_val, sizeof(double) * L.rq_nslots, cudaMemcpyDeviceToDevice, s), "copy");
+        }
+        rec_galerkin(L, N, L.Lg, L.rq_L, N.Lg, s);
+        rec_galerkin(L, N, L.Mg, L.rq_M, N.Mg, s);
     }
     ck(cudaGetLastError(), "split launches");
     h->split_valid = true;
@@ -855,9 +926,10 @@ void build_fast_t_graph(smg_hierarchy* h) {
     }
     for (int l = 0; l < h->H; l++) {
         DLevel& L = h->L[l];
-        kern::prep_level<<<blocks_for(L.nflat), kern::kThreads, 0, s>>>(L.nflat, L.n, L.vals, L.dinv, L.vals32,
-                                                                      L.dinv32);
+        kern::axpy_devt<<<blocks_for(L.rq_nslots), kern::kThreads, 0, s>>>(L.rq_nslots, h->t_fast, L.rq_L, L.rq_M,
+                                                                          L.rq_val);
     }
+    rec_prep_levels(h, s);
     record_coarsest_factor(h, s);
     ck(cudaGetLastError(), "fast t launches");
     ck(cudaStreamEndCapture(s, &g), "end capture fast t");
@@ -984,10 +1056,29 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
         L.pt_row = upload(h, lp.pt_row);
         L.pt_w = upload(h, lp.pt_w);
         L.pt_w32 = upload(h, to_f32(lp.pt_w));
+        L.rq_slices = upload(h, lp.rq_slices);
+        L.rq_nslices = (int)lp.rq_slices.size();
+        L.rq_row = upload(h, lp.rq_row);
+        L.rq_col = upload(h, lp.rq_col);
+        L.rq_val = upload(h, lp.rq_w);
+        L.rq_val32 = upload(h, to_f32(lp.rq_w));
+        L.rq_nslots = (int64_t)lp.rq_col.size();
+        L.rq_nq = (int64_t)lp.q_dst.size();
+        L.rq_npt = (int64_t)lp.pt_row.size();
+        L.q_dst = upload(h, lp.q_dst);
+        L.q_ptr = upload(h, lp.q_ptr);
+        L.q_src = upload(h, lp.q_src);
+        L.q_pw = upload(h, lp.q_pw);
+        L.q_nnz = (int64_t)lp.q_src.size();
         L.g_ptr = upload(h, lp.g_ptr);
         L.g_src = upload(h, lp.g_src);
-        L.g_w = upload(h, lp.g_w);
+        L.g_pw = upload(h, lp.g_pw);
         L.g_nnz = (int64_t)lp.g_src.size();
+        {
+            int R = 1;
+            while (R < 16 && (lp.rq_maxw + R - 1) / R > 8) R *= 2;
+            L.Rq = L.Rq32 = R;
+        }
     }
     const AssemblyPlan& A = P.asmb;
     h->nv = A.nv;
@@ -1395,8 +1486,7 @@ int smg_run_stage(smg_hierarchy* h, int stage, int level, int nrhs, int precisio
             }
             case SMG_STAGE_GALERKIN: {
                 DLevel& N = h->L[level + 1];
-                kern::galerkin<<<blocks_for(N.nflat), kern::kThreads, 0, s>>>(N.nflat, L.g_ptr, L.g_src, L.g_w,
-                                                                            L.vals, N.vals);
+                rec_galerkin(L, N, L.vals, L.rq_val, N.vals, s);
                 break;
             }
             case SMG_STAGE_FACTOR: record_coarsest_factor(h, s); break;
@@ -1407,6 +1497,17 @@ int smg_run_stage(smg_hierarchy* h, int stage, int level, int nrhs, int precisio
     ck(cudaGetLastError(), "stage launches");
     return SMG_OK;
     SMG_GUARD_END
+}
+
+int smg_level_restriction(const smg_hierarchy* h, int level, int64_t out[5]) {
+    if (!h || !out || level < 0 || level >= h->H) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    const DLevel& L = h->L[level];
+    out[0] = L.rq_nq;
+    out[1] = L.rq_npt;
+    out[2] = L.rq_nslots;
+    out[3] = L.Rq;
+    out[4] = L.Rq32;
+    return SMG_OK;
 }
 
 int smg_level_config(const smg_hierarchy* h, int level, int32_t out[4]) {

@@ -61,10 +61,21 @@ struct DLevel {
     int32_t* pt_row = nullptr;
     double* pt_w = nullptr;
     float* pt_w32 = nullptr;
-    int64_t* g_ptr = nullptr;
-    int32_t* g_src = nullptr;
-    double* g_w = nullptr;
-    int64_t g_nnz = 0;
+    // residual fused with restriction: RQSlice layout over the next level's rows,
+    // values [-P^T | Q = P^T A_l] (binary64 and binary32), lanes per row
+    RQSlice* rq_slices = nullptr;
+    int rq_nslices = 0;
+    int32_t* rq_row = nullptr;
+    int32_t* rq_col = nullptr;
+    double* rq_val = nullptr;
+    float* rq_val32 = nullptr;
+    double *rq_L = nullptr, *rq_M = nullptr;  // P^T L_l and P^T M_l in the same layout (fast t updates)
+    int64_t rq_nslots = 0, rq_nq = 0, rq_npt = 0;
+    int Rq = 8, Rq32 = 8;
+    // Galerkin stage 1 (Q = P^T A_l into rq_val) and stage 2 (A_{l+1} = Q P)
+    int32_t *q_dst = nullptr, *q_ptr = nullptr, *q_src = nullptr, *q_pw = nullptr;
+    int32_t *g_ptr = nullptr, *g_src = nullptr, *g_pw = nullptr;
+    int64_t g_nnz = 0, q_nnz = 0;
     // vectors, capacity n * kMaxRhs
     double *x = nullptr, *b = nullptr, *r = nullptr;
     float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;

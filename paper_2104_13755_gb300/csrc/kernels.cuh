@@ -210,49 +210,78 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) residual(con
         for (int q = 0; q < K; q++) r[(int64_t)row * K + q] = acc[q];
 }
 
-// Restriction r_{h+1} = P^T r_h (Alg. 2 "restrict residual") through the CSR of
-// P^T, four lanes per coarse row, plus the start of the coarse cycle's iterate.
-// That start is x_{h+1} = 0, and the first Gauss-Seidel colour step from it
+// Residual fused with restriction (Alg. 2 "compute residual", "restrict
+// residual"): b_{h+1} = P^T (b_h - A_h x_h) computed as P^T b_h - Q x_h with
+// Q = P^T A_h from the Galerkin stage 1, so one gather per coarse row replaces
+// the residual pass, its round trip through memory and the restriction pass.
+// Rows are coarse rows in the RQSlice layout (R lanes per row; entries k < wb
+// hold -P[i,I] against b_h, the rest Q[I,j] against x_h), so acc = init - sum
+// over all entries of value * vector.  The kernel also starts the coarse
+// iterate, x_{h+1} = 0, and the first Gauss-Seidel colour step from that zero
 // gives each row of colour class 0 (rows [0, nseed)) exactly b_i / a_ii (its
-// neighbours are all zero, and fma(-a, 0, b) = b), so with nseed > 0 this
-// kernel writes that value and the caller skips that colour step.
-template <typename T, int K>
-__global__ void __launch_bounds__(kThreads) restrict_rows(int nc, const int32_t* __restrict__ ptr,
-                                                          const int32_t* __restrict__ rows, const T* __restrict__ w,
-                                                          const T* __restrict__ r, T* __restrict__ bc,
-                                                          T* __restrict__ xc, const T* __restrict__ dinv_c,
-                                                          int nseed) {
-    constexpr int RR = 4, PREP = 4;
-    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) / RR);
-    const int sub = threadIdx.x % RR;
-    const int I = g < nc ? g : nc - 1;
-    const int k0 = ptr[I], k1 = ptr[I + 1];
-    int ri[PREP];
-    T wi[PREP];
+// neighbours are all zero, and fma(-a, 0, b) = b), so with nseed > 0 it writes
+// that value and the caller skips that colour step.
+template <typename T, int K, int R>
+__global__ void __launch_bounds__(kThreads) restrict_fused(const RQSlice* __restrict__ slices, int nslices,
+                                                           const int32_t* __restrict__ rq_row,
+                                                           const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                           const T* __restrict__ b, const T* __restrict__ x,
+                                                           T* __restrict__ bc, T* __restrict__ xc,
+                                                           const T* __restrict__ dinv_c, int nseed) {
+    constexpr int RL = 32 / R, PRE = 8;
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int s = w / R;
+    const int lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    const RQSlice m = slices[s];
+    const int sub = lane / RL;
+    const int r = (w % R) * RL + (lane % RL);
+    const int W = m.wb + m.wq;
+    const bool valid = r < m.nrows;
+    const int I = valid ? rq_row[m.pos0 + r] : 0;
+    int c[PRE];
+    T v[PRE];
 #pragma unroll
-    for (int u = 0; u < PREP; u++) {
-        const int k = k0 + sub + u * RR;
-        ri[u] = k < k1 ? rows[k] : 0;
-        wi[u] = k < k1 ? w[k] : T(0);
+    for (int u = 0; u < PRE; u++) {
+        const int k = sub + R * u;
+        if (k < W) {
+            c[u] = ldg(col + m.off + k * 32 + r);
+            v[u] = ldg(val + m.off + k * 32 + r);
+        }
     }
-    const T dseed = I < nseed ? dinv_c[I] : T(0);
+    const T dseed = (valid && I < nseed) ? dinv_c[I] : T(0);
     pdl_wait();
     pdl_trigger();
     T acc[K];
 #pragma unroll
     for (int q = 0; q < K; q++) acc[q] = T(0);
+    T g[PRE][K];
 #pragma unroll
-    for (int u = 0; u < PREP; u++)
+    for (int u = 0; u < PRE; u++) {
+        const int k = sub + R * u;
+        if (k < W) {
+            const T* src = k < m.wb ? b : x;
 #pragma unroll
-        for (int q = 0; q < K; q++) acc[q] += wi[u] * ldg(r + (int64_t)ri[u] * K + q);
-    for (int k = k0 + sub + PREP * RR; k < k1; k += RR)
+            for (int q = 0; q < K; q++) g[u][q] = ldg(src + (int64_t)c[u] * K + q);
+        }
+    }
 #pragma unroll
-        for (int q = 0; q < K; q++) acc[q] += w[k] * ldg(r + (int64_t)rows[k] * K + q);
+    for (int u = 0; u < PRE; u++)
+        if (sub + R * u < W)
 #pragma unroll
-    for (int o = RR / 2; o > 0; o >>= 1)
+            for (int q = 0; q < K; q++) acc[q] -= v[u] * g[u][q];
+    for (int k = sub + R * PRE; k < W; k += R) {
+        const int cc = ldg(col + m.off + k * 32 + r);
+        const T vv = ldg(val + m.off + k * 32 + r);
+        const T* src = k < m.wb ? b : x;
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] -= vv * ldg(src + (int64_t)cc * K + q);
+    }
+#pragma unroll
+    for (int o = 16; o >= RL; o >>= 1)
 #pragma unroll
         for (int q = 0; q < K; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-    if (g < nc && sub == 0)
+    if (valid && sub == 0)
 #pragma unroll
         for (int q = 0; q < K; q++) {
             bc[(int64_t)I * K + q] = acc[q];
@@ -802,15 +831,37 @@ __global__ void scatter_user(int64_t nflat, const int64_t* __restrict__ map, con
     vals[e] = k >= 0 ? user[k] : 0.0;
 }
 
-// Numeric Galerkin product A_{h+1} = P^T A_h P on the precomputed pattern: each
-// coarse entry gathers its fixed list of (fine entry, P_iI P_jJ) pairs.
-__global__ void galerkin(int64_t nflat_c, const int64_t* __restrict__ gp, const int32_t* __restrict__ src,
-                         const double* __restrict__ w, const double* __restrict__ fine, double* __restrict__ coarse) {
+// Numeric Galerkin product A_{h+1} = P^T A_h P (Eq. gca) on the precomputed
+// patterns, in two stages that are both fixed-order gathers (no atomics):
+// stage 1 forms Q = P^T A_h, one thread per entry of Q, each summing its
+// products P[i,I] A_h[i,j] over the fine rows i of P^T row I; stage 2 forms
+// A_{h+1} = Q P, one thread per coarse entry, summing Q[I,j] P[j,J] over the
+// columns j of Q row I.  Q stays in the slots of the fused residual-restriction
+// operator, which uses it in every cycle.
+__global__ void galerkin_q(int64_t nq, const int32_t* __restrict__ dst, const int32_t* __restrict__ ptr,
+                           const int32_t* __restrict__ src, const int32_t* __restrict__ pw,
+                           const double* __restrict__ fine, const double* __restrict__ p_w, double* __restrict__ rq) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nq) return;
+    double acc = 0.0;
+    for (int32_t k = ptr[e]; k < ptr[e + 1]; k++) acc = fma(ldg(p_w + pw[k]), ldg(fine + src[k]), acc);
+    rq[dst[e]] = acc;
+}
+
+__global__ void galerkin_qp(int64_t nflat_c, const int32_t* __restrict__ ptr, const int32_t* __restrict__ src,
+                            const int32_t* __restrict__ pw, const double* __restrict__ rq,
+                            const double* __restrict__ p_w, double* __restrict__ coarse) {
     const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= nflat_c) return;
     double acc = 0.0;
-    for (int64_t k = gp[d]; k < gp[d + 1]; k++) acc += w[k] * ldg(fine + src[k]);
+    for (int32_t k = ptr[d]; k < ptr[d + 1]; k++) acc = fma(ldg(rq + src[k]), ldg(p_w + pw[k]), acc);
     coarse[d] = acc;
+}
+
+// Binary32 copy of an array (the fused restriction operator of the mixed form).
+__global__ void copy_f32(int64_t m, const double* __restrict__ a, float* __restrict__ o) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) o[e] = (float)a[e];
 }
 
 // Reciprocal diagonal and the binary32 copies used by the mixed-precision cycle.

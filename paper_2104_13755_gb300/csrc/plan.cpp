@@ -457,31 +457,212 @@ int finalize_plan(Plan& p, std::string& err) {
                         fill[I]++;
                     }
         }
-        // Galerkin contributions, gathered per coarse row I: every fine row p with
-        // P[p, I] != 0 and every entry a_pq of that row adds P[p, I] a_pq P[q, J] to
-        // coarse entry (I, J) for each weight P[q, J] of row q.
+        std::vector<int32_t> fine_slice(n, 0);
+        for (size_t si = 0; si < lv.slices.size(); si++)
+            for (int k = 0; k < lv.slices[si].nrows; k++) fine_slice[lv.slices[si].row0 + k] = (int32_t)si;
+        // Entries of fine row pr as (column, flat index): the diagonal first, then
+        // the off-diagonal slots in ascending column order.
+        auto fine_row = [&](int32_t pr, std::vector<std::pair<int32_t, int32_t>>& out) {
+            out.clear();
+            out.emplace_back(pr, pr);
+            const SliceMeta& fs = lv.slices[fine_slice[pr]];
+            const int rl = pr - fs.row0;
+            for (int k = 0; k < fs.width; k++) {
+                const int64_t slot = slot_at(fs, rl, k);
+                const int32_t pc = lv.sell_col[slot];
+                if (pc != pr) out.emplace_back(pc, (int32_t)(lv.sbase + slot));
+            }
+        };
+        // Slot a of P row pr that holds coarse row I.
+        auto p_slot = [&](int32_t pr, int32_t I) -> int32_t {
+            for (int a = 0; a < 3; a++)
+                if (lv.p_w[a * n + pr] != 0.0 && lv.p_idx[a * n + pr] == I) return a;
+            return -1;
+        };
+        if (lv.sbase + lv.nslots > (int64_t)INT32_MAX || 3 * n > (int64_t)INT32_MAX) {
+            err = "level too large for 32-bit Galerkin indices";
+            return SMG_ERR_INVALID_ARG;
+        }
+        // ---- Q = P^T A_l: columns of coarse row I = the fine rows of P^T row I
+        // with their neighbours, ascending
+        std::vector<int32_t> qlen(nc, 0);
+        std::vector<std::vector<int32_t>> qcols_chunk;
+        std::vector<int64_t> qrp(nc + 1, 0);
+        std::vector<int32_t> qcols;
+        {
+            const int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+            const int64_t chunks = nc < 4096 ? 1 : nt;
+            qcols_chunk.assign(chunks, {});
+            std::vector<std::thread> th;
+            auto body = [&](int64_t c) {
+                const int64_t I0 = nc * c / chunks, I1 = nc * (c + 1) / chunks;
+                std::vector<int32_t> stamp(n, -1);
+                std::vector<std::pair<int32_t, int32_t>> row;
+                std::vector<int32_t> cols;
+                for (int64_t I = I0; I < I1; I++) {
+                    cols.clear();
+                    for (int32_t t = lv.pt_ptr[I]; t < lv.pt_ptr[I + 1]; t++) {
+                        fine_row(lv.pt_row[t], row);
+                        for (auto& e : row)
+                            if (stamp[e.first] != (int32_t)I) {
+                                stamp[e.first] = (int32_t)I;
+                                cols.push_back(e.first);
+                            }
+                    }
+                    std::sort(cols.begin(), cols.end());
+                    qlen[I] = (int32_t)cols.size();
+                    qcols_chunk[c].insert(qcols_chunk[c].end(), cols.begin(), cols.end());
+                }
+            };
+            for (int64_t c = 0; c + 1 < chunks; c++) th.emplace_back(body, c);
+            body(chunks - 1);
+            for (auto& x : th) x.join();
+            for (int64_t I = 0; I < nc; I++) qrp[I + 1] = qrp[I] + qlen[I];
+            qcols.reserve(qrp[nc]);
+            for (auto& v : qcols_chunk) {
+                qcols.insert(qcols.end(), v.begin(), v.end());
+                std::vector<int32_t>().swap(v);
+            }
+        }
+        // ---- layout: coarse rows by decreasing total width (ties: ascending row)
+        lv.rq_row.resize(nc);
+        std::iota(lv.rq_row.begin(), lv.rq_row.end(), 0);
+        auto ptlen = [&](int32_t I) { return lv.pt_ptr[I + 1] - lv.pt_ptr[I]; };
+        std::stable_sort(lv.rq_row.begin(), lv.rq_row.end(), [&](int32_t x, int32_t y) {
+            return ptlen(x) + qlen[x] > ptlen(y) + qlen[y];
+        });
+        lv.rq_slices.clear();
+        lv.rq_maxw = 0;
+        {
+            int64_t off = 0;
+            for (int64_t p0 = 0; p0 < nc; p0 += kSlice) {
+                RQSlice sl{};
+                sl.pos0 = (int32_t)p0;
+                sl.nrows = (int32_t)std::min<int64_t>(kSlice, nc - p0);
+                for (int r = 0; r < sl.nrows; r++) {
+                    const int32_t I = lv.rq_row[p0 + r];
+                    sl.wb = std::max(sl.wb, ptlen(I));
+                    sl.wq = std::max(sl.wq, qlen[I]);
+                }
+                if (off > (int64_t)INT32_MAX - (int64_t)(sl.wb + sl.wq) * kSlice) {
+                    err = "level too large for 32-bit restriction slots";
+                    return SMG_ERR_INVALID_ARG;
+                }
+                sl.off = (int32_t)off;
+                off += (int64_t)(sl.wb + sl.wq) * kSlice;
+                lv.rq_maxw = std::max(lv.rq_maxw, sl.wb + sl.wq);
+                lv.rq_slices.push_back(sl);
+            }
+            lv.rq_col.assign(off, 0);
+            lv.rq_w.assign(off, 0.0);
+        }
+        // position of every coarse row, and the stage-1 numbering of Q entries
+        // (coarse rows in layout order, columns ascending)
+        std::vector<int32_t> pos_of(nc);
+        for (int64_t p0 = 0; p0 < nc; p0++) pos_of[lv.rq_row[p0]] = (int32_t)p0;
+        std::vector<int64_t> qe0(nc + 1, 0);  // first Q entry of position p
+        for (int64_t p0 = 0; p0 < nc; p0++) qe0[p0 + 1] = qe0[p0] + qlen[lv.rq_row[p0]];
+        if (qe0[nc] > (int64_t)INT32_MAX) {
+            err = "Galerkin plan too large";
+            return SMG_ERR_INVALID_ARG;
+        }
+        lv.q_dst.assign(qe0[nc], 0);
+        for (const RQSlice& sl : lv.rq_slices)
+            for (int r = 0; r < kSlice; r++) {
+                const bool ok = r < sl.nrows;
+                const int32_t I = ok ? lv.rq_row[sl.pos0 + r] : 0;
+                const int32_t nb = ok ? ptlen(I) : 0, nq = ok ? qlen[I] : 0;
+                for (int k = 0; k < sl.wb; k++) {
+                    const int64_t slot = (int64_t)sl.off + (int64_t)k * kSlice + r;
+                    if (k < nb) {
+                        lv.rq_col[slot] = lv.pt_row[lv.pt_ptr[I] + k];
+                        lv.rq_w[slot] = -lv.pt_w[lv.pt_ptr[I] + k];
+                    } else {
+                        lv.rq_col[slot] = nb > 0 ? lv.pt_row[lv.pt_ptr[I]] : 0;
+                    }
+                }
+                for (int k = 0; k < sl.wq; k++) {
+                    const int64_t slot = (int64_t)sl.off + (int64_t)(sl.wb + k) * kSlice + r;
+                    lv.rq_col[slot] = k < nq ? qcols[qrp[I] + k] : (nq > 0 ? qcols[qrp[I]] : 0);
+                    if (k < nq) lv.q_dst[qe0[sl.pos0 + r] + k] = (int32_t)slot;
+                }
+            }
+        // ---- stage 1 contributions: Q[I, j] = sum over the fine rows pr of P^T
+        // row I (ascending) of P[pr, I] A_l[pr, j]
+        lv.q_ptr.assign(qe0[nc] + 1, 0);
+        std::atomic<bool> bad{false};
+        for (int pass = 0; pass < 2 && !bad; pass++) {
+            if (pass == 1) {
+                int64_t tot = 0;
+                for (int64_t e = 0; e < qe0[nc]; e++) {
+                    tot += lv.q_ptr[e + 1];
+                    if (tot > INT32_MAX - 1) {
+                        err = "Galerkin plan too large";
+                        return SMG_ERR_INVALID_ARG;
+                    }
+                    lv.q_ptr[e + 1] = (int32_t)tot;
+                }
+                lv.q_src.assign(tot, 0);
+                lv.q_pw.assign(tot, 0);
+            }
+            parallel_rows(nc, [&](int64_t I0, int64_t I1) {
+                std::vector<int32_t> loc(n, -1);
+                std::vector<std::pair<int32_t, int32_t>> row;
+                for (int64_t I = I0; I < I1 && !bad; I++) {
+                    const int64_t e0 = qe0[pos_of[I]];
+                    for (int64_t k = qrp[I]; k < qrp[I + 1]; k++) loc[qcols[k]] = (int32_t)(k - qrp[I]);
+                    for (int32_t t = lv.pt_ptr[I]; t < lv.pt_ptr[I + 1]; t++) {
+                        const int32_t pr = lv.pt_row[t];
+                        const int32_t a = p_slot(pr, (int32_t)I);
+                        if (a < 0) {
+                            bad = true;
+                            return;
+                        }
+                        fine_row(pr, row);
+                        for (auto& en : row) {
+                            const int64_t e = e0 + loc[en.first];
+                            if (pass == 0) {
+                                lv.q_ptr[e + 1]++;
+                            } else {
+                                const int32_t k = lv.q_ptr[e]++;
+                                lv.q_src[k] = en.second;
+                                lv.q_pw[k] = (int32_t)(a * n + pr);
+                            }
+                        }
+                    }
+                }
+            });
+            if (pass == 1) {  // the fill advanced every q_ptr[e] to the start of e + 1
+                for (int64_t e = qe0[nc]; e > 0; e--) lv.q_ptr[e] = lv.q_ptr[e - 1];
+                lv.q_ptr[0] = 0;
+            }
+        }
+        // ---- stage 2 contributions: A_{l+1}[I, J] = sum over Q row I (ascending
+        // fine column j) and the slots b of P row j with P[j, b] = J of Q[I, j] P[j, J]
         std::vector<int32_t> nx_slice_of_row;
         if (!nx.coarsest) {
             nx_slice_of_row.assign(nc, 0);
             for (size_t si = 0; si < nx.slices.size(); si++)
                 for (int k = 0; k < nx.slices[si].nrows; k++) nx_slice_of_row[nx.slices[si].row0 + k] = (int32_t)si;
         }
-        std::vector<int32_t> fine_slice(n, 0);
-        for (size_t si = 0; si < lv.slices.size(); si++)
-            for (int k = 0; k < lv.slices[si].nrows; k++) fine_slice[lv.slices[si].row0 + k] = (int32_t)si;
-        // two passes (count, fill); coarse rows are split across host threads, and
-        // every destination belongs to exactly one row, so the threads never share one
+        if (nx.nflat > (int64_t)INT32_MAX) {
+            err = "level too large for 32-bit Galerkin indices";
+            return SMG_ERR_INVALID_ARG;
+        }
         lv.g_ptr.assign(nx.nflat + 1, 0);
-        std::atomic<bool> bad{false};
         for (int pass = 0; pass < 2 && !bad; pass++) {
             if (pass == 1) {
-                for (int64_t d = 0; d < nx.nflat; d++) lv.g_ptr[d + 1] += lv.g_ptr[d];
-                if (lv.g_ptr[nx.nflat] > (int64_t)INT32_MAX) {
-                    err = "Galerkin plan too large";
-                    return SMG_ERR_INVALID_ARG;
+                int64_t tot = 0;
+                for (int64_t d = 0; d < nx.nflat; d++) {
+                    tot += lv.g_ptr[d + 1];
+                    if (tot > INT32_MAX - 1) {
+                        err = "Galerkin plan too large";
+                        return SMG_ERR_INVALID_ARG;
+                    }
+                    lv.g_ptr[d + 1] = (int32_t)tot;
                 }
-                lv.g_src.assign(lv.g_ptr[nx.nflat], 0);
-                lv.g_w.assign(lv.g_ptr[nx.nflat], 0.0);
+                lv.g_src.assign(tot, 0);
+                lv.g_pw.assign(tot, 0);
             }
             parallel_rows(nc, [&](int64_t I0, int64_t I1) {
                 std::vector<int32_t> stamp(nc, -1);
@@ -503,39 +684,29 @@ int finalize_plan(Plan& p, std::string& err) {
                         if (J == I) return I;
                         return stamp[J] == I ? slot_of[J] : -1;
                     };
-                    for (int32_t t = lv.pt_ptr[I]; t < lv.pt_ptr[I + 1]; t++) {
-                        const int32_t pr = lv.pt_row[t];
-                        const double wI = lv.pt_w[t];
-                        auto entry = [&](int32_t pc, int64_t e) {
-                            for (int b = 0; b < 3; b++) {
-                                double wb = lv.p_w[b * n + pc];
-                                if (wb == 0.0) continue;
-                                int64_t d = dst_of(lv.p_idx[b * n + pc]);
-                                if (d < 0) {
-                                    bad = true;
-                                    return;
-                                }
-                                if (pass == 0) lv.g_ptr[d + 1]++;
-                                else {
-                                    int64_t k = lv.g_ptr[d]++;
-                                    lv.g_src[k] = (int32_t)e;
-                                    lv.g_w[k] = wI * wb;
-                                }
+                    const int64_t e0 = qe0[pos_of[I]];
+                    for (int64_t k = qrp[I]; k < qrp[I + 1]; k++) {
+                        const int32_t j = qcols[k];
+                        const int32_t src = lv.q_dst[e0 + (k - qrp[I])];
+                        for (int bb = 0; bb < 3; bb++) {
+                            if (lv.p_w[bb * n + j] == 0.0) continue;
+                            const int64_t d = dst_of(lv.p_idx[bb * n + j]);
+                            if (d < 0) {
+                                bad = true;
+                                return;
                             }
-                        };
-                        entry(pr, pr);
-                        const SliceMeta& fs = lv.slices[fine_slice[pr]];
-                        const int rl = pr - fs.row0;
-                        for (int k = 0; k < fs.width; k++) {
-                            int64_t slot = slot_at(fs, rl, k);
-                            int32_t pc = lv.sell_col[slot];
-                            if (pc == pr) continue;
-                            entry(pc, lv.sbase + slot);
+                            if (pass == 0) {
+                                lv.g_ptr[d + 1]++;
+                            } else {
+                                const int32_t q = lv.g_ptr[d]++;
+                                lv.g_src[q] = src;
+                                lv.g_pw[q] = (int32_t)(bb * n + j);
+                            }
                         }
                     }
                 }
             });
-            if (pass == 1) {  // the fill advanced every g_ptr[d] to the start of d + 1
+            if (pass == 1) {
                 for (int64_t d = nx.nflat; d > 0; d--) lv.g_ptr[d] = lv.g_ptr[d - 1];
                 lv.g_ptr[0] = 0;
             }

@@ -26,6 +26,20 @@ struct SliceMeta {
 
 inline int64_t slot_at(const SliceMeta& s, int r, int k) { return (int64_t)s.off + (int64_t)k * kSlice + r; }
 
+// Slice header of the fused residual-restriction operator of a level (rows =
+// coarse rows): 32 consecutive positions [pos0, pos0 + nrows); entry k of the
+// position at local row r sits at slot off + 32 k + r: k < wb is the
+// restriction segment (applied to the fine right-hand side), wb <= k < wb + wq
+// the segment of Q = P^T A (applied to the fine iterate).
+struct RQSlice {
+    int32_t pos0;
+    int32_t nrows;
+    int32_t wb;
+    int32_t wq;
+    int32_t off;
+    int32_t pad;
+};
+
 struct LevelPlan {
     int64_t n = 0;
     bool coarsest = false;
@@ -53,11 +67,21 @@ struct LevelPlan {
     std::vector<double> p_w;
     std::vector<int32_t> pt_ptr, pt_row;
     std::vector<double> pt_w;
-    // Galerkin plan: next-level flat entry d = sum over k in [g_ptr[d], g_ptr[d+1]) of
-    // g_w[k] * flat_this[g_src[k]]
-    std::vector<int64_t> g_ptr;
-    std::vector<int32_t> g_src;
-    std::vector<double> g_w;
+    // Residual fused with restriction (Alg. 2 "restrict residual" as one product):
+    //   b_{l+1}[I] = sum_i P[i,I] b_l[i] - sum_j Q[I,j] x_l[j],  Q = P^T A_l,
+    // in the RQSlice layout: rq_row[position] = coarse row, rq_col per slot (fine
+    // row), rq_w per slot: -P[i,I] in the restriction segment, 0 in the Q
+    // segment (Q is numeric, written by the Galerkin stage 1) and in padding.
+    std::vector<RQSlice> rq_slices;
+    std::vector<int32_t> rq_row, rq_col;
+    std::vector<double> rq_w;
+    int32_t rq_maxw = 0;
+    // Galerkin product (Eq. gca) in two stages.  Stage 1, Q = P^T A_l: Q entry e
+    // (slot q_dst[e] of the layout above) = sum over k in [q_ptr[e], q_ptr[e+1])
+    // of flat_l[q_src[k]] * p_w[q_pw[k]].  Stage 2, A_{l+1} = Q P: next-level
+    // flat entry d = sum over k in [g_ptr[d], g_ptr[d+1]) of rq[g_src[k]] * p_w[g_pw[k]].
+    std::vector<int32_t> q_dst, q_ptr, q_src, q_pw;
+    std::vector<int32_t> g_ptr, g_src, g_pw;
     // flat index -> position in the natural CSR pattern (for read-back)
     std::vector<int64_t> flat_to_csr;
 };
