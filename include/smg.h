@@ -354,11 +354,21 @@ int  smg_residual_norms_noalloc(int64_t n, const int64_t *rowptr_dev, const int3
                                 int nrhs, double *out_dev, smg_stream stream);
 
 /* =====================================================================
- * Batches: many meshes (each with its own hierarchy) updated and solved by
- * one graph launch each, a branch per mesh, so the small coarse-level kernels
- * of different meshes overlap on the GPU.
+ * Batches: many meshes (each with its own hierarchy, sizes free) with nrhs
+ * right-hand sides each.  One graph launch updates every mesh (a branch per
+ * mesh); one persistent kernel launch solves every mesh: each mesh's Alg. 1
+ * loop of Alg. 2 cycles is a program of phases (colour steps, the fused
+ * residual-restriction, the coarsest products, prolongation, the stopping
+ * test) whose warp-sized work units the resident warps take from per-mesh
+ * device queues, so the small coarse-level phases of different meshes run
+ * side by side.  The persistent form needs the V-cycle solver, Gauss-Seidel
+ * and two levels or more on every mesh; otherwise (or in SMG_BATCH_GRAPH
+ * mode) the solve is one graph launch with a branch per mesh.
  * ===================================================================== */
 typedef struct smg_batch smg_batch;
+
+#define SMG_BATCH_PERSISTENT 0  /* default */
+#define SMG_BATCH_GRAPH      1
 
 /* Reference `count` hierarchies of the current device (they must outlive the
  * batch; options of a hierarchy are read when the batch first uses it). */
@@ -367,12 +377,17 @@ void smg_batch_destroy(smg_batch *batch);
 /* Offsets of mesh i in the concatenated vectors: unknowns [u[i], u[i+1]),
  * vertices [v[i], v[i+1]) (host arrays of count + 1). */
 int  smg_batch_offsets(const smg_batch *batch, int64_t *unknown_offsets, int64_t *vertex_offsets);
+/* Solve mode of later smg_batch_solve calls: SMG_BATCH_PERSISTENT or
+ * SMG_BATCH_GRAPH.  SMG_ERR_INVALID_ARG for another value. */
+int  smg_batch_set_mode(smg_batch *batch, int mode);
 /* smg_update_positions for every mesh: V_dev holds the meshes' positions
  * concatenated (vertex offsets x 3), one t for all. */
 int  smg_batch_update_positions(smg_batch *batch, const double *V_dev, double t, smg_stream stream);
 /* Solve every mesh: b_dev, x_dev concatenated (unknown offsets x nrhs,
  * row-major per mesh); infos (count entries) may be NULL.  Synchronises
- * `stream`; returns the first failing status over the meshes or SMG_OK. */
+ * `stream`; returns the first failing status over the meshes or SMG_OK;
+ * SMG_ERR_TIMEOUT when the persistent launch found no work to take for two
+ * seconds (a scheduling fault: the results are not valid). */
 int  smg_batch_solve(smg_batch *batch, const double *b_dev, double *x_dev, int nrhs, smg_info *infos,
                      smg_stream stream);
 

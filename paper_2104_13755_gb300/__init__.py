@@ -103,6 +103,7 @@ def _load():
         "smg_batch_offsets": (I32, [P, P, P]),
         "smg_batch_update_positions": (I32, [P, P, D, P]),
         "smg_batch_solve": (I32, [P, P, P, I32, P, P]),
+        "smg_batch_set_mode": (I32, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -413,9 +414,13 @@ class Hierarchy:
 
 
 class Batch:
-    """Several hierarchies (same device) updated and solved by one graph launch
-    each, one graph branch per mesh (smg_batch_*).  Vectors are the meshes'
-    unknown vectors concatenated; positions the meshes' vertices concatenated."""
+    """Several hierarchies (same device): one graph launch updates every mesh
+    (a branch per mesh); one persistent kernel launch solves every mesh
+    (mode "persistent", the default), or one graph launch with a branch per
+    mesh (mode "graph") (smg_batch_*).  Vectors are the meshes' unknown
+    vectors concatenated; positions the meshes' vertices concatenated."""
+
+    MODES = {"persistent": 0, "graph": 1}
 
     def __init__(self, hierarchies):
         self.hs = list(hierarchies)
@@ -438,6 +443,9 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def set_mode(self, mode):
+        _check(lib.smg_batch_set_mode(self._h, self.MODES[mode]), "smg_batch_set_mode")
 
     def update_positions(self, V, t, stream=None):
         _check(lib.smg_batch_update_positions(self._h, _dev_ptr(V), float(t), _stream_ptr(stream)),

@@ -496,6 +496,26 @@ cudaGraphExec_t cycle_graph(smg_hierarchy* h, int K, bool mixed) {
 // of 1, 2, 4, 8, 16 over timed forward sweeps (values are irrelevant to the
 // cost; the buffers hold zeros at this point).  Without tuning, the fewest
 // lanes leaving at most eight entries per lane in the widest slices.
+// Value for `level` of a per-level list in an environment variable ("R" for
+// every level, or "R0,R1,..."), 0 when unset or not one of 1, 2, 4, 8, 16.
+int env_lanes(const char* name, int level) {
+    const char* env = std::getenv(name);
+    if (!env) return 0;
+    std::string spec(env);
+    size_t pos = 0;
+    int r = 0;
+    for (int q = 0; q <= level && pos != std::string::npos; q++) {
+        r = std::atoi(spec.c_str() + pos);
+        size_t comma = spec.find(',', pos);
+        if (q < level) pos = comma == std::string::npos ? std::string::npos : comma + 1;
+    }
+    return (r == 1 || r == 2 || r == 4 || r == 8 || r == 16) ? r : 0;
+}
+
+// With SMG_LANES_PER_ROW set (a measurement aid: profilers serialise launches,
+// which changes what the timing would pick), the lanes of the smoother
+// (SMG_LANES_PER_ROW, SMG_LANES_PER_ROW_F32) and of the fused restriction
+// (SMG_RQ_LANES, SMG_RQ_LANES_F32) come from the environment instead.
 void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
     const char* env = std::getenv("SMG_LANES_PER_ROW");
     cudaEvent_t e0, e1;
@@ -513,16 +533,11 @@ void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
         int R = 1;
         while (R < 16 && (p90 + R - 1) / R > 8) R *= 2;
         L.R = L.R32 = R;
-        if (env) {  // "R" for every level, or "R0,R1,..." per level
-            std::string spec(env);
-            size_t pos = 0;
-            int r = 0;
-            for (int q = 0; q <= l && pos != std::string::npos; q++) {
-                r = std::atoi(spec.c_str() + pos);
-                size_t comma = spec.find(',', pos);
-                if (q < l) pos = comma == std::string::npos ? std::string::npos : comma + 1;
-            }
-            if (r == 1 || r == 2 || r == 4 || r == 8 || r == 16) L.R = L.R32 = r;
+        if (env) {
+            if (int r = env_lanes("SMG_LANES_PER_ROW", l)) L.R = L.R32 = r;
+            if (int r = env_lanes("SMG_LANES_PER_ROW_F32", l)) L.R32 = r;
+            if (int r = env_lanes("SMG_RQ_LANES", l)) L.Rq = L.Rq32 = r;
+            if (int r = env_lanes("SMG_RQ_LANES_F32", l)) L.Rq32 = r;
             continue;
         }
         if (!tune) continue;
@@ -1178,9 +1193,28 @@ cudaGraphExec_t build_batch_solve(smg_batch* B, bool mixed) {
     return exec;
 }
 
+// The persistent solve as a graph: schedule reset, the engine, the states copy.
+cudaGraphExec_t build_engine_graph(smg_batch* B, BatchEngine* E) {
+    cudaGraph_t g = nullptr;
+    ck(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "capture engine");
+    ck(engine_record(E, B->cap), "engine launch");
+    ck(cudaMemcpyAsync(B->states, engine_states(E), sizeof(SolveState) * B->hs.size(), cudaMemcpyDeviceToHost,
+                       B->cap), "states copy");
+    ck(cudaMemcpyAsync(B->engine_err, engine_error_flag(E), sizeof(int), cudaMemcpyDeviceToHost, B->cap),
+       "error copy");
+    ck(cudaStreamEndCapture(B->cap, &g), "end capture engine");
+    cudaGraphExec_t exec = nullptr;
+    ck(cudaGraphInstantiate(&exec, g, 0), "instantiate engine graph");
+    cudaGraphDestroy(g);
+    return exec;
+}
+
 void free_batch(smg_batch* B) {
     if (B->update_exec) cudaGraphExecDestroy(B->update_exec);
     for (auto& kv : B->solve_exec) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : B->engine_exec) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : B->engines) engine_destroy(kv.second);
+    if (B->engine_err) cudaFreeHost(B->engine_err);
     for (void* p : B->allocs) cudaFree(p);
     if (B->t_host) cudaFreeHost(B->t_host);
     if (B->states) cudaFreeHost(B->states);
@@ -1196,6 +1230,10 @@ int fail(const std::string& msg, int code) {
 #define SMG_GUARD_END                                      \
     }                                                      \
     catch (const CudaFail& e) {                            \
+        return fail(e.what(), SMG_ERR_CUDA);               \
+    }                                                      \
+    catch (const std::runtime_error& e) {                  \
+        cudaGetLastError();                                \
         return fail(e.what(), SMG_ERR_CUDA);               \
     }                                                      \
     catch (const std::bad_alloc&) {                        \
@@ -1571,6 +1609,8 @@ int smg_batch_create(smg_hierarchy* const* hs, int count, smg_batch** out) {
         B->t_dev = balloc<double>(B, 1);
         ck(cudaMallocHost((void**)&B->t_host, sizeof(double)), "cudaMallocHost");
         ck(cudaMallocHost((void**)&B->states, sizeof(SolveState) * count), "cudaMallocHost");
+        ck(cudaMallocHost((void**)&B->engine_err, sizeof(int)), "cudaMallocHost");
+        *B->engine_err = 0;
         build_batch_update(B);
     } catch (const CudaFail& e) {
         free_batch(B);
@@ -1629,9 +1669,16 @@ int smg_batch_solve(smg_batch* B, const double* b, double* x, int nrhs, smg_info
     SMG_GUARD_BEGIN
     const bool mixed = B->hs[0]->opts.precision == SMG_MIXED;
     const int key = (mixed ? 16 : 0) + nrhs;
-    auto it = B->solve_exec.find(key);
+    const bool persistent = B->mode == SMG_BATCH_PERSISTENT && engine_supported(B);
+    auto it = persistent ? B->engine_exec.find(key) : B->solve_exec.find(key);
     cudaGraphExec_t e;
-    if (it != B->solve_exec.end()) e = it->second;
+    if (persistent && it != B->engine_exec.end()) e = it->second;
+    else if (persistent) {
+        BatchEngine* E = engine_create(B, nrhs, mixed);
+        B->engines[key] = E;
+        e = build_engine_graph(B, E);
+        B->engine_exec[key] = e;
+    } else if (it != B->solve_exec.end()) e = it->second;
     else {
         switch (nrhs) {
             case 1: e = build_batch_solve<1>(B, mixed); break;
@@ -1647,6 +1694,9 @@ int smg_batch_solve(smg_batch* B, const double* b, double* x, int nrhs, smg_info
     ck(cudaGraphLaunch(e, s), "batch solve");
     ck(cudaMemcpyAsync(x, B->stage_x, bytes, cudaMemcpyDeviceToDevice, s), "copy x back");
     ck(cudaStreamSynchronize(s), "sync");
+    if (persistent && *B->engine_err)
+        return fail("persistent batch solve: no work unit could be taken for the idle limit", SMG_ERR_TIMEOUT);
+    if (persistent) engine_trace(B->engines[key], B->states);
     int worst = SMG_OK;
     for (size_t i = 0; i < B->hs.size(); i++) {
         const SolveState& ss = B->states[i];
@@ -1663,6 +1713,12 @@ int smg_batch_solve(smg_batch* B, const double* b, double* x, int nrhs, smg_info
     if (worst != SMG_OK) return fail("a mesh of the batch did not converge or was not SPD", worst);
     return SMG_OK;
     SMG_GUARD_END
+}
+
+int smg_batch_set_mode(smg_batch* B, int mode) {
+    if (!B || (mode != SMG_BATCH_PERSISTENT && mode != SMG_BATCH_GRAPH)) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    B->mode = mode;
+    return SMG_OK;
 }
 
 int smg_lumped_mass(smg_hierarchy* h, const double* V, double* m, smg_stream stream) {

@@ -148,7 +148,12 @@ struct smg_hierarchy {
     int tail_cluster = 0;        // CTAs per tail cluster (0 = clusters unavailable)
 };
 
-// Several hierarchies solved by one graph launch (a branch per mesh).
+namespace smg {
+struct BatchEngine;  // engine.cu: persistent batched solve
+}
+
+// Several hierarchies updated by one graph launch (a branch per mesh) and
+// solved by one persistent launch (or one graph launch with a branch per mesh).
 struct smg_batch {
     std::vector<smg_hierarchy*> hs;        // referenced, owned by the caller
     std::vector<int64_t> uoff, voff;       // unknown / vertex offsets of the concatenated vectors
@@ -161,11 +166,26 @@ struct smg_batch {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t update_exec = nullptr;
     std::map<int, cudaGraphExec_t> solve_exec;
+    std::map<int, smg::BatchEngine*> engines;  // key precision * 16 + nrhs
+    std::map<int, cudaGraphExec_t> engine_exec;
+    int* engine_err = nullptr;             // pinned: error flag of the last persistent solve
+    int mode = 0;                          // SMG_BATCH_PERSISTENT or SMG_BATCH_GRAPH
     std::vector<void*> allocs;
     int device = 0;
 };
 
 namespace smg {
+// engine.cu: the persistent batched solve of every mesh of a batch (V-cycle
+// solver, Gauss-Seidel smoother, at least two levels per mesh)
+bool engine_supported(const smg_batch* B);
+BatchEngine* engine_create(smg_batch* B, int K, bool mixed);  // throws on failure
+void engine_destroy(BatchEngine* E);
+// resets the schedule and launches the solve, then gathers every mesh's state
+cudaError_t engine_record(BatchEngine* E, cudaStream_t s);
+const int* engine_error_flag(const BatchEngine* E);
+const SolveState* engine_states(const BatchEngine* E);
+int engine_grid(const BatchEngine* E);
+void engine_trace(const BatchEngine* E, const SolveState* host_states);
 // dense.cu: record the coarsest factorisation (Cholesky, then the inverse factor
 // and its transpose) on `s`; launches only, capturable.
 void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s);

@@ -15,7 +15,8 @@ def test_captured_traffic_follows_the_kernel_region(monkeypatch):
     changed = dict(bench.TRAFFIC_CAPTURE, sha256="0" * 64)
     monkeypatch.setattr(bench, "TRAFFIC_CAPTURE", changed)
     assert bench.captured_traffic() is None
-    missing = dict(bench.TRAFFIC_CAPTURE, region=("no such marker", "// Damped Jacobi update"))
+    missing = dict(bench.TRAFFIC_CAPTURE, regions=(("paper_2104_13755_gb300/csrc/kernels.cuh", "no such marker",
+                                                     "// Damped Jacobi update"),))
     monkeypatch.setattr(bench, "TRAFFIC_CAPTURE", missing)
     assert bench.captured_traffic() is None
 

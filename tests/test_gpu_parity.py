@@ -266,10 +266,9 @@ def test_cluster_tail_and_launch_paths_match_oracle(tail, nrhs, monkeypatch):
     c.h.close()
 
 
-def test_batch_matches_individual_solves_and_oracle():
-    """a11: uneven meshes (spheres, tori, a Dirichlet disk) with 3 right-hand
-    sides each, updated and solved by one graph launch; every mesh must equal
-    its own stand-alone solve and the oracle."""
+@pytest.fixture(scope="module")
+def batch_cases():
+    """Uneven meshes (spheres, tori, a Dirichlet disk) for the batched form."""
     meshes = [synth.perturbed_icosphere(3, seed=1), synth.torus(48, 20, seed=2),
               synth.perturbed_geodesic_sphere(14, seed=3), synth.torus(90, 30, seed=4)]
     Vd, Fd, bnd = synth.disk(40, seed=5)
@@ -277,16 +276,32 @@ def test_batch_matches_individual_solves_and_oracle():
     for V, F in meshes:
         cases.append(Case(V, F, 1e-2, max_coarse=300))
     cases.append(Case(Vd, Fd, 1e-2, mask=bnd, max_coarse=300))
+    return cases
+
+
+def _batch(cases, mode, **opts):
+    """A batch of the cases' hierarchies with `opts` (the batch reads them at its
+    first solve), positions uploaded and updated."""
+    for c in cases:
+        c.h.set_options(**opts)
+    batch = smg.Batch([c.h for c in cases])
+    batch.set_mode(mode)
+    batch.update_positions(torch.from_numpy(np.concatenate([c.V for c in cases])).cuda(), 1e-2)
+    return batch
+
+
+def test_batch_matches_individual_solves_and_oracle(batch_cases):
+    """a11, graph mode: uneven meshes with 3 right-hand sides each, updated and
+    solved by one graph launch (a branch per mesh); every mesh must equal its
+    own stand-alone solve bit for bit, and the oracle."""
+    cases = batch_cases
     batch = smg.Batch([c.h for c in cases])
     Vcat = torch.from_numpy(np.concatenate([c.V for c in cases])).cuda()
     batch.update_positions(Vcat, 1e-2)
     bs = [synth.uniform_rhs(c.n, nrhs=3, seed=20 + i) for i, c in enumerate(cases)]
     for prec in (smg.FP64, smg.MIXED):
-        for c in cases:
-            c.h.set_options(rtol=1e-10, precision=prec)
         batch.close()
-        batch = smg.Batch([c.h for c in cases])
-        batch.update_positions(Vcat, 1e-2)
+        batch = _batch(cases, "graph", rtol=1e-10, precision=prec)
         x, infos = batch.solve(to_dev(np.concatenate(bs)))
         xs = x.cpu().numpy()
         u = batch.unknown_offsets
@@ -303,6 +318,78 @@ def test_batch_matches_individual_solves_and_oracle():
     for c in cases:
         c.h.set_options(rtol=1e-10, precision=smg.FP64)
     batch.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_batch_persistent_every_cycle(batch_cases, nrhs):
+    """a11, persistent mode: one kernel launch runs every cycle of every mesh
+    from its own work queue; after k cycles (k = 1, 2, 4) every mesh's iterate
+    equals the oracle's cycle k entry by entry (1e-12), and solved to 1e-10
+    every mesh takes the oracle's cycle count."""
+    cases = batch_cases
+    bs = [synth.uniform_rhs(c.n, nrhs=nrhs, seed=40 + i) for i, c in enumerate(cases)]
+    bcat = to_dev(np.concatenate(bs))
+    refs = [oracle.solve(c.levels, b, opt=oracle.Options(rtol=1e-30, max_cycles=4), keep_iterates=True)
+            for c, b in zip(cases, bs)]
+    for k in (1, 2, 4):
+        batch = _batch(cases, "persistent", rtol=1e-30, max_cycles=k, precision=smg.FP64)
+        x, infos = batch.solve(bcat, check=False)
+        xs = x.cpu().numpy()
+        u = batch.unknown_offsets
+        for i, c in enumerate(cases):
+            assert infos[i]["cycles"] == k
+            xo = refs[i].iterates[k - 1]
+            assert maxrel(xs[u[i]:u[i + 1]], xo) <= CYCLE_TOL, (i, k)
+        batch.close()
+    batch = _batch(cases, "persistent", rtol=1e-10, max_cycles=100, precision=smg.FP64)
+    x, infos = batch.solve(bcat)
+    xs = x.cpu().numpy()
+    u = batch.unknown_offsets
+    for i, c in enumerate(cases):
+        ref = oracle.solve(c.levels, bs[i], opt=oracle.Options(rtol=1e-10))
+        assert infos[i]["cycles"] == ref.cycles
+        assert maxrel(xs[u[i]:u[i + 1]], ref.x) <= CYCLE_TOL
+    batch.close()
+    for c in cases:
+        c.h.set_options(rtol=1e-10, max_cycles=100, precision=smg.FP64)
+
+
+def test_batch_persistent_mixed_every_step(batch_cases):
+    """a11 with form 1: binary32 cycles inside binary64 refinement, every mesh
+    in the persistent launch, each refinement step against the oracle's
+    binary32 refinement (MIXED_STEP_TOL of the step's correction), and
+    solved to 1e-10 against the graph mode's cycle counts (+-1) and a direct
+    solve (1e-9)."""
+    cases = batch_cases
+    bs = [synth.uniform_rhs(c.n, nrhs=3, seed=60 + i) for i, c in enumerate(cases)]
+    bcat = to_dev(np.concatenate(bs))
+    refs = [oracle.solve_mixed(c.levels, b, opt=oracle.Options(rtol=1e-30, max_cycles=3), keep_iterates=True)
+            for c, b in zip(cases, bs)]
+    for k in (1, 2, 3):
+        batch = _batch(cases, "persistent", rtol=1e-30, max_cycles=k, precision=smg.MIXED)
+        x, infos = batch.solve(bcat, check=False)
+        xs = x.cpu().numpy()
+        u = batch.unknown_offsets
+        for i, c in enumerate(cases):
+            assert infos[i]["cycles"] == k
+            xo = refs[i].iterates[k - 1]
+            prev = refs[i].iterates[k - 2] if k > 1 else np.zeros_like(xo)
+            gap = np.abs(xs[u[i]:u[i + 1]] - xo).max()
+            assert gap <= MIXED_STEP_TOL * np.abs(xo - prev).max() + 1e-13 * np.abs(xo).max(), (i, k)
+        batch.close()
+    out = {}
+    for mode in ("persistent", "graph"):
+        batch = _batch(cases, mode, rtol=1e-10, max_cycles=100, precision=smg.MIXED)
+        x, infos = batch.solve(bcat)
+        out[mode] = (x.cpu().numpy(), [d["cycles"] for d in infos], batch.unknown_offsets)
+        batch.close()
+    xs, cyc, u = out["persistent"]
+    for i, c in enumerate(cases):
+        assert abs(cyc[i] - out["graph"][1][i]) <= 1
+        xd = spla.splu(c.A.tocsc()).solve(bs[i])
+        assert rel(xs[u[i]:u[i + 1]], xd) <= 1e-9
+    for c in cases:
+        c.h.set_options(rtol=1e-10, max_cycles=100, precision=smg.FP64)
 
 
 def test_fast_t_updates_match_oracle_galerkin_chain():
