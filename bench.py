@@ -12,7 +12,15 @@ solve from x = 0 to the tolerance.  value = V-cycles per second over the timed
 steps (time per step = time to 1e-9 including the update).  L2 is flushed by a
 256 MB write before every timed step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+The same line carries, under "configs", the other workloads of the method's
+forms, each timed the same way on this GPU: the plain binary64 solve on a
+perturbed icosphere split 4 times (2,562 vertices, 3 levels, to 1e-10), the
+batched form (64 meshes of 10k-200k vertices x 3 right-hand sides), the mixed
+precision form at 2.62M vertices (2 right-hand sides, to 1e-10), the
+differentiable solve on a 400 x 400 Dirichlet disk (forward + adjoint) and
+per-frame re-solves of a deforming 655k-vertex icosphere (p50 / p99).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--headline-only]
 
 Under torchrun (N > 1) every rank solves its own replica of the workload (the
 path of one mesh does not shard); the value adds all ranks' cycles over the
@@ -43,31 +51,66 @@ METRIC = "V-cycles/s at 1M verts (solve to rel. residual 1e-9, update included)"
 L2_FLUSH_BYTES = 256 << 20
 
 
-# DRAM traffic of the roofline kernel from one ncu capture (profiles/
-# gs_colour_level0_torus1m.md): dram__bytes_read.sum + dram__bytes_write.sum of
-# the level-0 binary64 colour launches, per sweep (4 classes x 28.13 MB).  Valid
-# only for the kernel source it was taken on; reported as null otherwise.
+# DRAM traffic of the level-0 sweep from one ncu capture: dram__bytes_read.sum
+# + dram__bytes_write.sum of the level-0 binary64 colour launches, per sweep
+# (4 classes x 28.13 MB).  Valid only for the kernel source it was taken on;
+# reported as null otherwise.
 TRAFFIC_CAPTURE = dict(bytes_per_sweep=28134144 + 28132352 + 28132864 + 28132864, bytes_per_launch=28.13e6,
-                       source="paper_2104_13755_gb300/csrc/kernels.cuh",
-                       region=("constexpr int kThreads = 256;", "// Damped Jacobi update"),
+                       regions=(("paper_2104_13755_gb300/csrc/rowslice.cuh", "constexpr int kThreads = 256;",
+                                 "}  // namespace kern"),
+                                ("paper_2104_13755_gb300/csrc/kernels.cuh",
+                                 "// ---------------------------------------------------------------------------\n"
+                                 "// Multicolour Gauss-Seidel", "// Damped Jacobi update")),
                        sha256="09dc140ecb4867825f4cf277ac496b5156cdb6ea80da30788ba1a28eb9f53f18")
 
 
 def captured_traffic():
     """The captured per-sweep traffic while the source of the measured kernel
-    (the sweep kernel and the helpers it uses, a fixed region of the header) is
-    the one that was captured; None once it has changed."""
+    (the sweep kernel and the row helpers it uses: fixed regions of two
+    headers, hashed in order) is the one that was captured; None once it has
+    changed."""
     import hashlib
+    text = ""
     try:
-        with open(os.path.join(ROOT, TRAFFIC_CAPTURE["source"])) as f:
-            text = f.read()
-        first, last = TRAFFIC_CAPTURE["region"]
-        a, b = text.index(first), text.index(last)
-        if hashlib.sha256(text[a:b].encode()).hexdigest() != TRAFFIC_CAPTURE["sha256"]:
-            return None
+        for path, first, last in TRAFFIC_CAPTURE["regions"]:
+            with open(os.path.join(ROOT, path)) as f:
+                src = f.read()
+            a = src.index(first)
+            text += src[a:src.index(last, a)]
     except (OSError, ValueError):
         return None
+    if hashlib.sha256(text.encode()).hexdigest() != TRAFFIC_CAPTURE["sha256"]:
+        return None
     return TRAFFIC_CAPTURE["bytes_per_sweep"]
+
+
+# DRAM traffic of one binary64 V(2,2) cycle of the 1M-vertex torus from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum summed over every kernel
+# of one plain cycle graph, caches kept warm between kernels as in a solve).
+# Valid only while the kernel and layout sources are the ones captured (a hash
+# over the CUDA and plan sources); null otherwise or before a capture exists.
+CYCLE_TRAFFIC = dict(bytes_per_cycle=None, sha256=None)
+CYCLE_SOURCES = ("*.cu", "*.cuh", "*.hpp", "plan.cpp")
+
+
+def source_hash():
+    """sha256 over the kernel and layout sources of the library, in name order."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2104_13755_gb300", "csrc")
+    files = sorted({f for pat in CYCLE_SOURCES for f in glob.glob(os.path.join(csrc, pat))})
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_cycle_traffic():
+    if CYCLE_TRAFFIC["bytes_per_cycle"] is None or CYCLE_TRAFFIC["sha256"] != source_hash():
+        return None
+    return CYCLE_TRAFFIC["bytes_per_cycle"]
 
 
 def load_peaks():
@@ -193,7 +236,23 @@ def oracle_cycle_rate(V, F, b, w, plan, cycles_per_solve, sample_cycles):
         x = oracle.vcycle(levels, 0, np.ascontiguousarray(x), b, oracle.Options())
     tc = (time.perf_counter() - t0) / sample_cycles
     per_solve = tm["update_s"] + cycles_per_solve * tc
-    return cycles_per_solve / per_solve, tm, tc
+    return cycles_per_solve / per_solve, tm, tc, levels
+
+
+def oracle_omp_cycle_rate(levels, b, update_s, cycles_per_solve, sample_cycles):
+    """The oracle's cycle with its colour classes, residual and transfers run
+    in parallel on all host cores (App. "Multi-Color Gauss Seidel"), timed on
+    `sample_cycles` cycles; the update is the oracle's own (one thread)."""
+    import oracle
+    import oracle.omp as omp
+    ol = omp.OmpLevels(levels)
+    x = omp.vcycle(ol, 0, np.zeros_like(b), b, oracle.Options())  # first touch, thread start
+    t0 = time.perf_counter()
+    for _ in range(sample_cycles):
+        x = omp.vcycle(ol, 0, x, b, oracle.Options())
+    tc = (time.perf_counter() - t0) / sample_cycles
+    per_solve = update_s + cycles_per_solve * tc
+    return cycles_per_solve / per_solve, tc, omp.threads()
 
 
 # ---------------------------------------------------------------------------
@@ -267,9 +326,11 @@ def run_ours(args, w, rank, world, local_rank):
             torch.cuda.synchronize()
             h.solve_result()
             # the solve graph's WHILE node hides its kernels from kernel profilers;
-            # one plain cycle graph of each precision exposes them
+            # one plain cycle graph of each precision exposes them (own NVTX range each)
+            torch.cuda.nvtx.range_push("smg_cycle_" + ("f64" if p == smg.FP64 else "mixed"))
             h.run_stage("cycle", precision=p)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
         torch.cuda.nvtx.range_pop()
         h.close()
         return None
@@ -418,6 +479,8 @@ def run_ours(args, w, rank, world, local_rank):
                    "colours": [plan.level_info(l)[2] for l in range(plan.num_levels)],
                    "lanes_per_row_f64": [h.level_config(l)[0] for l in range(plan.num_levels - 1)],
                    "lanes_per_row_f32": [h.level_config(l)[1] for l in range(plan.num_levels - 1)],
+                   "restriction": [dict(zip(("q_entries", "pt_entries", "slots", "lanes_f64", "lanes_f32"),
+                                            h.level_restriction(l))) for l in range(plan.num_levels - 1)],
                    "cluster_tail_from_level": {"f64": h.cycle_config()[1], "f32": h.cycle_config()[2],
                                                "ctas": h.cycle_config()[3]},
                    "t": w["t"], "rtol": w["rtol"], "nrhs": w["nrhs"], "cycle": "V(2,2) multicolour GS",
@@ -433,12 +496,18 @@ def run_ours(args, w, rank, world, local_rank):
                   "refinement_steps_per_solve": cyc_mx[0]},
         "pcg": pcg,
         "ablation": ablation,
-        "roofline": {"kernel": "gs_colour<double,1> level-0 sweep (all colour launches)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": captured_traffic(), "traffic_source": "ncu dram__bytes_read.sum + "
-                     "dram__bytes_write.sum per sweep (profiles/gs_colour_level0_torus1m.md)",
+        "roofline": {"kernel": "one binary64 V(2,2) cycle (graph of every kernel of Alg. 2 on every level, "
+                               "the cluster tail and the coarsest solve)", "bound": "hbm",
+                     "achieved": cb64 / (cyc64_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": cb64 / (cyc64_ms * 1e-3) / 1e9 / peak, "traffic": captured_cycle_traffic(),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the kernels "
+                                       "of one plain cycle graph",
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                     "bytes_per_sweep": sb},
+                     "bytes_per_cycle": cb64, "cycle_us": cyc64_ms * 1e3},
+        "roofline_sweep_l0": {"kernel": "gs_colour<double,1> level-0 sweep (all colour launches)", "bound": "hbm",
+                              "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                              "traffic": captured_traffic(), "traffic_source": "ncu dram__bytes_read.sum + "
+                              "dram__bytes_write.sum per sweep", "bytes_per_sweep": sb},
         "roofline_vcycle": {"fp64": {"bytes": cb64, "achieved": cb64 / (cyc64_ms * 1e-3) / 1e9,
                                      "frac": cb64 / (cyc64_ms * 1e-3) / 1e9 / peak},
                             "mixed_inner": {"bytes": cb32, "achieved": cb32 / (cyc32_ms * 1e-3) / 1e9,
@@ -449,11 +518,18 @@ def run_ours(args, w, rank, world, local_rank):
         "gpu_launches": gpu_launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, tm, tc = oracle_cycle_rate(V, F, b, w, plan, cycles[0], sample_cycles=2)
+        rate, tm, tc, olev = oracle_cycle_rate(V, F, b, w, plan, cycles[0], sample_cycles=2)
         res["cpu_baseline"] = {"value": rate, "unit": "V-cycles/s", "cores": 1, "kind": "oracle",
                                "sample": "oracle update of the full workload (assembly %.1fs, Galerkin %.1fs, "
                                          "Cholesky %.1fs) + 2 V-cycles (%.2fs each), extrapolated to %d cycles"
-                                         % (tm["assembly_s"], tm["galerkin_s"], tm["cholesky_s"], tc, cycles[0])}
+                                         % (tm["assembly_s"], tm["galerkin_s"], tm["cholesky_s"], tc, cycles[0]),
+                               "cycle_only_per_s": 1.0 / tc}
+        orate, otc, nth = oracle_omp_cycle_rate(olev, b, tm["update_s"], cycles[0], sample_cycles=8)
+        res["cpu_baseline_allcores"] = {
+            "value": orate, "unit": "V-cycles/s", "cores": nth, "kind": "oracle, multicolour OpenMP cycle",
+            "sample": "8 V-cycles of the full workload (%.1f ms each) on %d threads, plus the oracle's own update "
+                      "(one thread, %.1f s), extrapolated to %d cycles" % (otc * 1e3, nth, tm["update_s"], cycles[0]),
+            "cycle_only_per_s": 1.0 / otc}
     h.close()
     return res
 
@@ -476,87 +552,169 @@ def batch_meshes(count=64, seed=2, lo=1e4, hi=2e5):
     return out
 
 
-def run_batch(args, rank, world, local_rank):
+def _timed(stream, flush, fn, reps):
+    """CUDA-event time (ms) of fn() on `stream` for each of `reps` runs, L2
+    flushed before each."""
+    import torch
+    out = []
+    for i in range(reps):
+        flush.fill_(i)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        out.append((a.elapsed_time(e), r))
+    return out
+
+
+def config_c1(args, dev, flush):
+    """Plain binary64 solve: perturbed icosphere split 4 times (2,562 vertices,
+    radius 1 + 0.1 x seeded spherical-harmonic noise), A = M + 1e-3 L, one RHS
+    uniform in [-1, 1], 3 levels (ratio 0.25), V(2,2) to rel. residual 1e-10.
+    Step = update + solve; the oracle solves the same system on one host thread."""
+    import torch
+    import oracle
+    import paper_2104_13755_gb300 as smg
+    V, F = synth.perturbed_icosphere(4, seed=0)
+    t, rtol = 1e-3, 1e-10
+    t0 = time.perf_counter()
+    plan = smg.Plan(V, F, max_levels=3, min_coarse=0)
+    h = smg.Hierarchy(plan, rtol=rtol, max_cycles=100, max_levels=3, min_coarse=0)
+    setup_s = time.perf_counter() - t0
+    n = plan.level_info(0)[0]
+    b = synth.uniform_rhs(n, seed=1)
+    Vd = torch.from_numpy(V).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h.update_positions(Vd, t)
+        return h.solve(bd)
+
+    forms = {}
+    for name, prec in (("f64", smg.FP64), ("mixed", smg.MIXED)):
+        h.set_options(rtol=rtol, max_cycles=100, precision=prec)
+        for _ in range(args.warmup):
+            step()
+        runs = _timed(stream, flush, step, args.steps)
+        x, info = runs[-1][1]
+        forms[name] = {"time_to_tol_ms": statistics.median([r[0] for r in runs]), "cycles": info["cycles"],
+                       "rel_residual": info["rel_residual"], "x": x.cpu().numpy()}
+    # the oracle on the same hierarchy (one host thread)
+    t0 = time.perf_counter()
+    A = oracle.system_matrix(V, F, t)
+    levels = oracle.build_levels(A, [plan.prolongation_csr(l) for l in range(1, plan.num_levels)])
+    ref = oracle.solve(levels, b, opt=oracle.Options(rtol=rtol))
+    cpu_s = time.perf_counter() - t0
+    for f in forms.values():
+        xg = f.pop("x")
+        f["max_rel_diff_vs_oracle"] = float(np.abs(xg - ref.x).max() / np.abs(ref.x).max())
+    h.close()
+    return {"metric": "time to rel. residual 1e-10, icosphere split 4 (2,562 vertices, update included)",
+            "value": forms["f64"]["time_to_tol_ms"], "unit": "ms", "higher_is_better": False, "dtype": "f64",
+            "config": {"workload": "icosphere4-2562-3levels", "n_vertices": int(V.shape[0]),
+                       "levels": [plan.level_info(l)[0] for l in range(plan.num_levels)], "t": t, "rtol": rtol,
+                       "l2": "flushed by a 256 MB write before every timed step"},
+            "setup_s": setup_s, "forms": forms, "oracle_cycles": ref.cycles,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": cpu_s * 1e3, "unit": "ms",
+                             "sample": "the oracle's whole update (assembly, Galerkin, Cholesky) and solve to 1e-10"}}
+
+
+def batch_meshes(count=64, seed=2, lo=1e4, hi=2e5):
+    """Seeded batch: sizes log-uniform in [lo, hi]; even entries perturbed geodesic
+    spheres (10 f^2 + 2 vertices), odd entries tori (R = 1, r = 0.3, 2% noise)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        if i % 2 == 0:
+            f = max(2, int(round(np.sqrt((n - 2) / 10.0))))
+            V, F = synth.perturbed_geodesic_sphere(f, seed=100 + i)
+        else:
+            u = max(8, int(round(np.sqrt(n * 1.0 / 0.3))))
+            v = max(4, int(round(n / u)))
+            V, F = synth.torus(u, v, seed=100 + i)
+        out.append((V, F))
+    return out
+
+
+def config_c2(args, dev, flush):
     """Batched form: 64 meshes x 3 right-hand sides b = M X (implicit smoothing of the
     coordinates), A = M + 1e-2 L, coarsest <= 1000, rtol 1e-9; one graph launch
     updates all meshes and one solves them, against the same meshes one by one."""
     import concurrent.futures
     import torch
     import paper_2104_13755_gb300 as smg
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
     meshes = batch_meshes()
     t0 = time.perf_counter()
     with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
         plans = list(ex.map(lambda m: smg.Plan(m[0], m[1], max_coarse=1000), meshes))
-    setup_s = time.perf_counter() - t0
     hs = [smg.Hierarchy(p, rtol=1e-9, max_cycles=200) for p in plans]
+    setup_s = time.perf_counter() - t0
     Vcat = torch.from_numpy(np.concatenate([m[0] for m in meshes])).to(dev)
     batch = smg.Batch(hs)
     batch.update_positions(Vcat, 1e-2)
     bl = [h.apply_mass(torch.from_numpy(np.ascontiguousarray(m[0])).to(dev)) for h, m in zip(hs, meshes)]
     bcat = torch.cat(bl)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     res = {}
     for name, prec in (("f64", smg.FP64), ("mixed", smg.MIXED)):
         for h in hs:
             h.set_options(rtol=1e-9, max_cycles=200, precision=prec)
-        batch.close()
-        batch = smg.Batch(hs)
-        batch.update_positions(Vcat, 1e-2)
-        for _ in range(args.warmup):
+        row = {}
+        for mode in ("persistent", "graph"):
+            batch.close()
+            batch = smg.Batch(hs)
+            batch.set_mode(mode)
             batch.update_positions(Vcat, 1e-2)
-            batch.solve(bcat)
-        bt, cyc = [], 0
-        for i in range(args.steps):
-            flush.fill_(i)
-            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            batch.update_positions(Vcat, 1e-2)
-            _, infos = batch.solve(bcat)
-            e.record(stream)
-            torch.cuda.synchronize()
-            bt.append(a.elapsed_time(e))
-            cyc = sum(d["cycles"] for d in infos)
-        # the same meshes one after another through the single-mesh API
-        st = []
-        for i in range(max(1, args.steps // 2)):
-            flush.fill_(i)
-            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            off = batch.vertex_offsets
+            for _ in range(args.warmup):
+                batch.update_positions(Vcat, 1e-2)
+                batch.solve(bcat)
+
+            def bstep():
+                batch.update_positions(Vcat, 1e-2)
+                return batch.solve(bcat)[1]
+
+            runs = _timed(stream, flush, bstep, args.steps)
+            upd = _timed(stream, flush, lambda: batch.update_positions(Vcat, 1e-2), max(3, args.steps // 4))
+            row[mode + "_ms"] = statistics.median([r[0] for r in runs])
+            row[mode + "_update_ms"] = statistics.median([r[0] for r in upd])
+            row[mode + "_cycles_total"] = sum(d["cycles"] for d in runs[-1][1])
+        off = batch.vertex_offsets
+
+        def sstep():
             for k, (h, b) in enumerate(zip(hs, bl)):
                 h.update_positions(Vcat[off[k]:off[k + 1]], 1e-2)
                 h.solve(b)
-            e.record(stream)
-            torch.cuda.synchronize()
-            st.append(a.elapsed_time(e))
-        res[name] = {"batched_ms": statistics.median(bt), "sequential_ms": statistics.median(st),
-                     "cycles_total": cyc, "speedup_vs_sequential": statistics.median(st) / statistics.median(bt)}
+
+        seq = _timed(stream, flush, sstep, max(1, args.steps // 4))
+        row["sequential_ms"] = statistics.median([r[0] for r in seq])
+        row["batched_ms"] = row["persistent_ms"]
+        row["speedup_vs_sequential"] = row["sequential_ms"] / row["persistent_ms"]
+        res[name] = row
     batch.close()
+    for h in hs:
+        h.close()
     nv = int(sum(m[0].shape[0] for m in meshes))
-    return {"metric": "batched time to rel. residual 1e-9 (64 meshes x 3 RHS, update included)",
-            "value": res["f64"]["batched_ms"], "unit": "ms", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": res["f64"]["batched_ms"], "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    return {"metric": "batched time to rel. residual 1e-9 (64 meshes x 3 RHS, update included; one graph "
+                      "launch updates all meshes, one persistent launch solves them)",
+            "value": res["f64"]["batched_ms"], "unit": "ms", "higher_is_better": False, "dtype": "f64",
             "config": {"workload": "batch64-3rhs", "meshes": len(meshes), "n_vertices_total": nv,
                        "sizes": [int(m[0].shape[0]) for m in meshes], "t": 1e-2, "rtol": 1e-9,
                        "l2": "flushed by a 256 MB write before every timed step"},
             "setup_s": setup_s, "forms": res}
 
 
-def run_icosphere9(args, rank, world, local_rank):
+def config_c3(args, dev, flush):
     """Mixed-precision form at 2.62M vertices: perturbed icosphere split 9 times,
     A = M + 1e-4 L, 2 RHS uniform in [-1, 1], rtol 1e-10; each step = update +
     solve from zero, binary64 V-cycles, binary32 cycles in binary64 refinement,
-    and both as CG preconditioners.  Also the level-0 binary64 sweep against the
-    measured HBM peak at a size where the level's matrix (~220 MB) cannot stay in
-    L2 (L2 flushed before every timed run)."""
+    and both as CG preconditioners.  Also the level-0 binary64 sweep and the
+    binary64 cycle against the measured HBM peak at a size where the level's
+    matrix (~220 MB) cannot stay in L2 (L2 flushed before every timed run)."""
     import torch
     import paper_2104_13755_gb300 as smg
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
     V, F = synth.perturbed_icosphere(9, seed=3)
     t, rtol = 1e-4, 1e-10
     t0 = time.perf_counter()
@@ -566,7 +724,6 @@ def run_icosphere9(args, rank, world, local_rank):
     Vd = torch.from_numpy(V).to(dev)
     bd = torch.from_numpy(synth.uniform_rhs(V.shape[0], nrhs=2, seed=7)).to(dev)
     h.update_positions(Vd, t)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     forms, xs = {}, {}
     for name, prec, solver in (("f64", smg.FP64, smg.VCYCLE), ("mixed", smg.MIXED, smg.VCYCLE),
@@ -575,51 +732,90 @@ def run_icosphere9(args, rank, world, local_rank):
         for _ in range(args.warmup):
             h.update_positions(Vd, t)
             h.solve(bd)
-        ts = []
-        for i in range(args.steps):
-            flush.fill_(i)
-            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+
+        def step():
             h.update_positions(Vd, t)
-            x, info = h.solve(bd)
-            e.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(e))
+            return h.solve(bd)
+
+        runs = _timed(stream, flush, step, max(3, args.steps // 2))
+        x, info = runs[-1][1]
         xs[name] = x.clone()
-        forms[name] = {"time_to_tol_ms": statistics.median(ts), "cycles": info["cycles"],
+        forms[name] = {"time_to_tol_ms": statistics.median([r[0] for r in runs]), "cycles": info["cycles"],
                        "rel_residual": info["rel_residual"]}
     ref = xs["f64"]
     for name in forms:
         forms[name]["rel_diff_vs_f64"] = float((xs[name] - ref).norm() / ref.norm())
     h.set_options(rtol=rtol, max_cycles=300, precision=smg.FP64, solver=smg.VCYCLE)
-    sw = []
-    for i in range(5):
-        flush.fill_(i)
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        h.run_stage("sweep", level=0, nrhs=2)
-        e.record(stream)
-        torch.cuda.synchronize()
-        sw.append(a.elapsed_time(e))
+    sw = [r[0] for r in _timed(stream, flush, lambda: h.run_stage("sweep", level=0, nrhs=2), 5)]
+    cyc = [r[0] / 4 for r in _timed(stream, flush, lambda: h.run_stage("cycle", nrhs=2, count=4), 5)]
     n0, z0 = plan.level_info(0)[:2]
+    levels = [(plan.level_info(l)[0], plan.level_info(l)[1]) for l in range(plan.num_levels)]
     peak, psrc = load_peaks()
     sweep_b = sweep_bytes(n0, z0, k=2)
+    cyc_b = cycle_bytes(levels, s=8, k=2)
     achieved = sweep_b / (statistics.median(sw) / 1e3) / 1e9
-    levels = [plan.level_info(l)[0] for l in range(plan.num_levels)]
+    ach_c = cyc_b / (statistics.median(cyc) / 1e3) / 1e9
     h.close()
-    return {"metric": "time to rel. residual 1e-10 at 2.62M verts, 2 RHS (update included)",
-            "value": forms["mixed"]["time_to_tol_ms"], "unit": "ms", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": forms["mixed"]["time_to_tol_ms"], "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
-            "config": {"workload": "icosphere9-2.62M-2rhs", "n_vertices": int(V.shape[0]), "levels": levels,
-                       "t": t, "rtol": rtol, "l2": "flushed by a 256 MB write before every timed step"},
+    return {"metric": "time to rel. residual 1e-10 at 2.62M verts, 2 RHS (mixed precision, update included)",
+            "value": forms["mixed"]["time_to_tol_ms"], "unit": "ms", "higher_is_better": False,
+            "dtype": "f32 inner / f64 outer",
+            "config": {"workload": "icosphere9-2.62M-2rhs", "n_vertices": int(V.shape[0]),
+                       "levels": [l[0] for l in levels], "t": t, "rtol": rtol,
+                       "l2": "flushed by a 256 MB write before every timed step"},
             "setup_s": setup_s, "forms": forms,
             "roofline_sweep_l0": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                   "frac": achieved / peak, "bytes_per_sweep": sweep_b,
-                                  "sweep_us": statistics.median(sw) * 1e3, "peak_source": psrc, "traffic": None}}
+                                  "sweep_us": statistics.median(sw) * 1e3, "peak_source": psrc},
+            "roofline_vcycle_f64": {"bound": "hbm", "achieved": ach_c, "peak": peak, "unit": "GB/s",
+                                    "frac": ach_c / peak, "bytes_per_cycle": cyc_b,
+                                    "cycle_us": statistics.median(cyc) * 1e3}}
 
 
-def run_frames(args, rank, world, local_rank):
+def config_c4(args, dev, flush):
+    """Differentiable solve on a 400 x 400 grid mapped to the unit disk (160,000
+    vertices, 1,596 Dirichlet boundary vertices), t = (mean edge length)^2:
+    loss ||x||^2_M with (M + t L) x = M e_s; a step is the forward solve and
+    the adjoint (a second solve and the per-face derivative kernels) giving
+    the gradients in V, t and b, to rel. residual 1e-10."""
+    import torch
+    import paper_2104_13755_gb300 as smg
+    V, F, bnd = synth.disk(400, seed=4)
+    u = np.flatnonzero(~bnd)
+    t = synth.mean_edge_length(V, F) ** 2
+    s = int(np.random.default_rng(104).integers(u.size))
+    t0 = time.perf_counter()
+    plan = smg.Plan(V, F, dirichlet=bnd)
+    h = smg.Hierarchy(plan, rtol=1e-10, max_cycles=200)
+    setup_s = time.perf_counter() - t0
+    e_s = torch.zeros(u.size, dtype=torch.float64, device=dev)
+    e_s[s] = 1.0
+    Vd = torch.from_numpy(V).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        Vt = Vd.clone().requires_grad_(True)
+        tt = torch.tensor(t, dtype=torch.float64, device=dev, requires_grad=True)
+        m = smg.differentiable_mass(h, Vt)
+        x = smg.differentiable_solve(h, Vt, tt, m * e_s)
+        loss = (m * x * x).sum()
+        loss.backward()
+        return Vt.grad, tt.grad
+
+    for _ in range(args.warmup):
+        step()
+    runs = _timed(stream, flush, step, max(3, args.steps // 2))
+    gV, gt = runs[-1][1]
+    h.close()
+    return {"metric": "forward + adjoint time, 400 x 400 Dirichlet disk (gradients in V, t, b)",
+            "value": statistics.median([r[0] for r in runs]), "unit": "ms", "higher_is_better": False,
+            "dtype": "f64",
+            "config": {"workload": "disk400-160k-dirichlet-adjoint", "n_vertices": int(V.shape[0]),
+                       "unknowns": int(u.size), "t": t, "rtol": 1e-10,
+                       "l2": "flushed by a 256 MB write before every timed step"},
+            "setup_s": setup_s, "grad_t": float(gt.item()), "grad_V_norm": float(gV.norm().item())}
+
+
+def config_c5(args, dev, flush):
     """Per-frame re-solve on a deforming mesh: perturbed icosphere split 8 times
     (655,362 vertices) moved each frame by a seeded sinusoidal displacement
     (amplitude 0.05); per frame: positions from pinned host memory to the GPU,
@@ -628,21 +824,22 @@ def run_frames(args, rank, world, local_rank):
     Latency per frame = host wall clock from the copy to the solve's status."""
     import torch
     import paper_2104_13755_gb300 as smg
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
     V0, F = synth.perturbed_icosphere(8, seed=5)
     t, rtol, nframes = 1e-3, 1e-8, 100
+    t0 = time.perf_counter()
     plan = smg.Plan(V0, F)
     h = smg.Hierarchy(plan, rtol=rtol, max_cycles=200)
+    setup_s = time.perf_counter() - t0
     Vh = torch.empty((V0.shape[0], 3), dtype=torch.float64).pin_memory()
     Vd = torch.empty((V0.shape[0], 3), dtype=torch.float64, device=dev)
+    frames = [torch.from_numpy(synth.sinusoidal_displacement(V0, f, seed=11)) for f in range(nframes)]
     forms = {}
     for name, prec in (("f64", smg.FP64), ("mixed", smg.MIXED)):
         h.set_options(rtol=rtol, max_cycles=200, precision=prec)
         x = None
         lat, cyc = [], []
         for f in range(-args.warmup, nframes):
-            Vh.copy_(torch.from_numpy(synth.sinusoidal_displacement(V0, f % nframes, seed=11)))
+            Vh.copy_(frames[f % nframes])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             Vd.copy_(Vh, non_blocking=True)
@@ -661,12 +858,30 @@ def run_frames(args, rank, world, local_rank):
                        "cycles_max": int(max(cyc))}
     h.close()
     return {"metric": "per-frame latency p50 (re-assembly, Galerkin, factor, warm solve to 1e-8, 3 RHS)",
-            "value": forms["mixed"]["p50_ms"], "unit": "ms", "n_gpus": world, "steps": nframes,
-            "warmup": args.warmup, "ms_per_step": forms["mixed"]["p50_ms"], "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "value": forms["mixed"]["p50_ms"], "unit": "ms", "higher_is_better": False,
+            "dtype": "f32 inner / f64 outer",
             "config": {"workload": "icosphere8-655k-100-frames", "n_vertices": int(V0.shape[0]), "t": t,
                        "rtol": rtol, "frames": nframes, "h2d_bytes_per_frame": int(V0.shape[0] * 24)},
-            "forms": forms}
+            "setup_s": setup_s, "forms": forms}
+
+
+CONFIGS = {"c1_icosphere4": config_c1, "c2_batch64": config_c2, "c3_icosphere9_mixed": config_c3,
+           "c4_disk400_adjoint": config_c4, "c5_frames655": config_c5}
+WORKLOAD_FLAGS = {"ico2562": "c1_icosphere4", "batch64": "c2_batch64", "ico262": "c3_icosphere9_mixed",
+                  "disk160": "c4_disk400_adjoint", "frames655": "c5_frames655"}
+
+
+def run_configs(args, local_rank, names):
+    import torch
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    out = {}
+    for name in names:
+        t0 = time.perf_counter()
+        out[name] = CONFIGS[name](args, dev, flush)
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def run_reference(args, w, rank, world):
@@ -676,7 +891,7 @@ def run_reference(args, w, rank, world):
     import paper_2104_13755_gb300 as smg
     import oracle
     V, F, b = make_workload(w)
-    plan = smg.Plan(V, F)
+    plan = smg.Plan(V, F)  # the hierarchy P_1..P_H (host setup, no GPU), which the oracle takes as data
     tm = {}
     levels = oracle_levels(V, F, w["t"], plan, tm)
     ref = oracle.solve(levels, b, opt=oracle.Options(rtol=w["rtol"], max_cycles=200))
@@ -712,31 +927,41 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--small", action="store_true", help="40k-vertex torus (profiling captures)")
-    ap.add_argument("--workload", default="torus1m", choices=["torus1m", "batch64", "ico262", "frames655"],
-                    help="torus1m: the headline line; batch64: the batched multi-mesh form; ico262: the "
-                         "2.62M-vertex mixed-precision form; frames655: per-frame re-solves on a deforming mesh")
+    ap.add_argument("--workload", default="torus1m", choices=["torus1m"] + sorted(WORKLOAD_FLAGS),
+                    help="torus1m: the headline line (with every other workload under \"configs\"); "
+                         "ico2562, batch64, ico262, disk160, frames655: one of those workloads on its own line")
+    ap.add_argument("--headline-only", action="store_true", help="the 1M-vertex torus line without \"configs\"")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="run one step of each precision inside the NVTX range smg_profile and exit")
     ap.add_argument("--lanes", default=None,
                     help="lanes per matrix row per level, e.g. 1,2,4,8,8 (skips the autotuner; for profiling)")
+    ap.add_argument("--lanes-f32", default=None, help="the same for the binary32 kernels (with --lanes)")
+    ap.add_argument("--rq-lanes", default=None, help="lanes per row of the fused restriction, per level (with --lanes)")
+    ap.add_argument("--rq-lanes-f32", default=None, help="the same for binary32 (with --lanes)")
+    ap.add_argument("--tail", default=None, help="first level of the cluster tail (skips its tuning; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     w = SMALL if args.small else WORKLOAD
     if args.lanes:
         os.environ["SMG_LANES_PER_ROW"] = args.lanes
+        for flag, var in ((args.lanes_f32, "SMG_LANES_PER_ROW_F32"), (args.rq_lanes, "SMG_RQ_LANES"),
+                          (args.rq_lanes_f32, "SMG_RQ_LANES_F32")):
+            if flag:
+                os.environ[var] = flag
+    if args.tail:
+        os.environ["SMG_TAIL_LEVEL"] = args.tail
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         res = run_reference(args, w, rank, world)
-    elif args.workload == "batch64":
-        res = run_batch(args, rank, world, local_rank)
-    elif args.workload == "ico262":
-        res = run_icosphere9(args, rank, world, local_rank)
-    elif args.workload == "frames655":
-        res = run_frames(args, rank, world, local_rank)
+    elif args.workload != "torus1m":
+        name = WORKLOAD_FLAGS[args.workload]
+        res = dict(run_configs(args, local_rank, [name])[name], n_gpus=world, steps=args.steps,
+                   warmup=args.warmup, scaling="weak", vs_baseline=None, data="synthetic")
+        res["ms_per_step"] = res["value"]
     else:
         if world > 1:
             import torch
@@ -744,6 +969,9 @@ def main():
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl")
         res = run_ours(args, w, rank, world, local_rank)
+        if res is not None and world == 1 and not args.headline_only and not args.small:
+            # the other workloads, each on this rank's GPU (replicas under torchrun)
+            res["configs"] = run_configs(args, local_rank, list(CONFIGS))
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

@@ -23,5 +23,23 @@ def build(force=False):
     return LIB
 
 
+OMP_LIB = os.path.join(HERE, "_lib", "liboracle_omp.so")
+OMP_SRC = os.path.join(HERE, "smg_omp.c")
+
+
+def build_omp(force=False):
+    """The multicolour OpenMP loops (all-cores CPU baseline), same flags plus -fopenmp."""
+    os.makedirs(os.path.dirname(OMP_LIB), exist_ok=True)
+    if not force and os.path.exists(OMP_LIB) and os.path.getmtime(OMP_LIB) >= os.path.getmtime(OMP_SRC):
+        return OMP_LIB
+    tmp = OMP_LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
+           OMP_SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, OMP_LIB)
+    return OMP_LIB
+
+
 if __name__ == "__main__":
     print(build(force=True))
+    print(build_omp(force=True))
