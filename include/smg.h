@@ -380,6 +380,12 @@ int  smg_batch_offsets(const smg_batch *batch, int64_t *unknown_offsets, int64_t
 /* Solve mode of later smg_batch_solve calls: SMG_BATCH_PERSISTENT or
  * SMG_BATCH_GRAPH.  SMG_ERR_INVALID_ARG for another value. */
 int  smg_batch_set_mode(smg_batch *batch, int mode);
+/* Watchdog of the persistent launch: a warp that finds no work unit to take
+ * for `seconds` (default 2; every unit takes microseconds) makes the launch
+ * stop and the solve return SMG_ERR_TIMEOUT.  0 makes every warp give up at
+ * its first idle moment (exercises the timeout path; results not valid).
+ * seconds in [0, 60], else SMG_ERR_INVALID_ARG. */
+int  smg_batch_set_wait_limit(smg_batch *batch, double seconds);
 /* smg_update_positions for every mesh: V_dev holds the meshes' positions
  * concatenated (vertex offsets x 3), one t for all. */
 int  smg_batch_update_positions(smg_batch *batch, const double *V_dev, double t, smg_stream stream);

@@ -104,6 +104,7 @@ def _load():
         "smg_batch_update_positions": (I32, [P, P, D, P]),
         "smg_batch_solve": (I32, [P, P, P, I32, P, P]),
         "smg_batch_set_mode": (I32, [P, I32]),
+        "smg_batch_set_wait_limit": (I32, [P, D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -446,6 +447,10 @@ class Batch:
 
     def set_mode(self, mode):
         _check(lib.smg_batch_set_mode(self._h, self.MODES[mode]), "smg_batch_set_mode")
+
+    def set_wait_limit(self, seconds):
+        """Watchdog of the persistent launch (seconds a warp may find no work)."""
+        _check(lib.smg_batch_set_wait_limit(self._h, float(seconds)), "smg_batch_set_wait_limit")
 
     def update_positions(self, V, t, stream=None):
         _check(lib.smg_batch_update_positions(self._h, _dev_ptr(V), float(t), _stream_ptr(stream)),

@@ -1715,6 +1715,16 @@ int smg_batch_solve(smg_batch* B, const double* b, double* x, int nrhs, smg_info
     SMG_GUARD_END
 }
 
+int smg_batch_set_wait_limit(smg_batch* B, double seconds) {
+    if (!B || !(seconds >= 0.0) || seconds > 60.0) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    B->wait_ns = (long long)(seconds * 1e9);
+    for (auto& kv : B->engine_exec) cudaGraphExecDestroy(kv.second);  // rebuilt with the new limit
+    for (auto& kv : B->engines) engine_destroy(kv.second);
+    B->engine_exec.clear();
+    B->engines.clear();
+    return SMG_OK;
+}
+
 int smg_batch_set_mode(smg_batch* B, int mode) {
     if (!B || (mode != SMG_BATCH_PERSISTENT && mode != SMG_BATCH_GRAPH)) return fail("invalid argument", SMG_ERR_INVALID_ARG);
     B->mode = mode;

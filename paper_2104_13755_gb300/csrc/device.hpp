@@ -170,6 +170,7 @@ struct smg_batch {
     std::map<int, cudaGraphExec_t> engine_exec;
     int* engine_err = nullptr;             // pinned: error flag of the last persistent solve
     int mode = 0;                          // SMG_BATCH_PERSISTENT or SMG_BATCH_GRAPH
+    long long wait_ns = 2000000000ll;      // idle limit of a warp of the persistent launch
     std::vector<void*> allocs;
     int device = 0;
 };

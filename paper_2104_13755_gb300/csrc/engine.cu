@@ -507,6 +507,7 @@ struct BatchEngine {
     long long* trace = nullptr;    // launch start and every mesh's finish time (globaltimer)
     int32_t* home = nullptr;       // mesh served by each warp of the launch
     int nmesh = 0, K = 1, grid = 0, minb = 2;
+    long long idle_ns = 0;         // a warp that finds no unit for this long reports a timeout
 };
 
 namespace {
@@ -608,6 +609,7 @@ BatchEngine* engine_create(smg_batch* B, int K, bool mixed) {
     try {
         E->nmesh = (int)B->hs.size();
         E->K = K;
+        E->idle_ns = B->wait_ns;
         std::vector<eng::EMesh> meshes(E->nmesh);
         for (int i = 0; i < E->nmesh; i++) {
             smg_hierarchy* h = B->hs[i];
@@ -717,9 +719,6 @@ void engine_destroy(BatchEngine* E) {
     delete E;
 }
 
-// Idle limit of a warp that finds no unit to take anywhere before it reports a
-// timeout (every unit takes microseconds; a whole batched solve milliseconds).
-constexpr long long kEngineIdleLimitNs = 2000000000ll;
 
 cudaError_t engine_record(BatchEngine* E, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(E->ctl, 0, sizeof(eng::ECtl) * E->nmesh, s);
@@ -728,7 +727,7 @@ cudaError_t engine_record(BatchEngine* E, cudaStream_t s) {
     const dim3 grid(E->grid), block(256);
     SMG_ENG_K(E->K, E->minb,
               (eng::engine<KK, MB><<<grid, block, 0, s>>>(E->meshes, E->nmesh, E->home, E->ctl, E->counters,
-                                                           E->counters + 32, kEngineIdleLimitNs)));
+                                                           E->counters + 32, E->idle_ns)));
     copy_states<<<(E->nmesh + 127) / 128, 128, 0, s>>>(E->meshes, E->nmesh, E->states);
     return cudaGetLastError();
 }

@@ -392,6 +392,30 @@ def test_batch_persistent_mixed_every_step(batch_cases):
         c.h.set_options(rtol=1e-10, max_cycles=100, precision=smg.FP64)
 
 
+def test_batch_persistent_watchdog_reports_timeout(batch_cases):
+    """Failure detection without a GPU fault: with the persistent launch's idle
+    limit at zero every warp gives up at its first moment without work, the
+    launch ends, and the solve reports SMG_ERR_TIMEOUT; with the limit back at
+    two seconds the same batch solves correctly in the same context."""
+    cases = batch_cases
+    bs = [synth.uniform_rhs(c.n, nrhs=1, seed=80 + i) for i, c in enumerate(cases)]
+    bcat = to_dev(np.concatenate(bs))
+    batch = _batch(cases, "persistent", rtol=1e-10, max_cycles=100, precision=smg.FP64)
+    batch.set_wait_limit(0.0)
+    st = smg.lib.smg_batch_solve(batch._h, smg._dev_ptr(bcat), smg._dev_ptr(torch.zeros_like(bcat)), 1, None,
+                                 smg._stream_ptr(None))
+    assert st == 7 and b"idle" in smg.lib.smg_last_error()
+    batch.set_wait_limit(2.0)
+    x, infos = batch.solve(bcat)
+    xs = x.cpu().numpy()
+    u = batch.unknown_offsets
+    for i, c in enumerate(cases):
+        ref = oracle.solve(c.levels, bs[i], opt=oracle.Options(rtol=1e-10))
+        assert infos[i]["cycles"] == ref.cycles
+        assert maxrel(xs[u[i]:u[i + 1]], ref.x) <= CYCLE_TOL
+    batch.close()
+
+
 def test_fast_t_updates_match_oracle_galerkin_chain():
     """App. "Fast Data Smoothing": update_t forms every level from the kept
     P^T M P and P^T L P; each level must equal the oracle's Galerkin chain of
