@@ -18,7 +18,8 @@ perturbed icosphere split 4 times (2,562 vertices, 3 levels, to 1e-10), the
 batched form (64 meshes of 10k-200k vertices x 3 right-hand sides), the mixed
 precision form at 2.62M vertices (2 right-hand sides, to 1e-10), the
 differentiable solve on a 400 x 400 Dirichlet disk (forward + adjoint) and
-per-frame re-solves of a deforming 655k-vertex icosphere (p50 / p99).
+per-frame re-solves of a deforming 655k-vertex icosphere (p50 / p99), and a
+3|V| system (block size 3) on a 200k-vertex torus.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--headline-only]
 
@@ -865,10 +866,58 @@ def config_c5(args, dev, flush):
             "setup_s": setup_s, "forms": forms}
 
 
+def config_f3(args, dev, flush):
+    """3|V| system (block size 3, Sec. 6): torus 800 x 250 (200k vertices, 600k
+    unknowns), (M + 1e-3 L) (x) I_3 on the pattern of 3 x 3 blocks, one RHS
+    uniform in [-1, 1], to rel. residual 1e-9, binary64 and mixed; the sweep
+    runs in 3 x 3 blocks, one launch per vertex colour class.  Also the warm
+    level-0 sweep."""
+    import torch
+    import paper_2104_13755_gb300 as smg
+    V, F = synth.torus(800, 250, seed=7)
+    t0 = time.perf_counter()
+    plan = smg.Plan(V, F, block_size=3)
+    h = smg.Hierarchy(plan, rtol=1e-9, max_cycles=200)
+    setup_s = time.perf_counter() - t0
+    Vd = torch.from_numpy(V).to(dev)
+    n = plan.level_info(0)[0]
+    bd = torch.from_numpy(synth.uniform_rhs(n, seed=3)).to(dev)
+    stream = torch.cuda.current_stream()
+    forms = {}
+    for name, prec in (("f64", smg.FP64), ("mixed", smg.MIXED)):
+        h.set_options(rtol=1e-9, max_cycles=200, precision=prec)
+        for _ in range(args.warmup):
+            h.update_positions(Vd, 1e-3)
+            h.solve(bd)
+
+        def step():
+            h.update_positions(Vd, 1e-3)
+            return h.solve(bd)
+
+        runs = _timed(stream, flush, step, max(3, args.steps // 2))
+        x, info = runs[-1][1]
+        h.run_stage("sweep", level=0, precision=prec, count=2)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.run_stage("sweep", level=0, precision=prec, count=10)
+        e.record(stream)
+        torch.cuda.synchronize()
+        forms[name] = {"time_to_tol_ms": statistics.median([r[0] for r in runs]), "cycles": info["cycles"],
+                       "rel_residual": info["rel_residual"], "sweep_l0_us": a.elapsed_time(e) / 10 * 1e3}
+    classes = [plan.level_info(l)[2] for l in range(plan.num_levels)]
+    h.close()
+    return {"metric": "time to rel. residual 1e-9, 3|V| system on a 200k-vertex torus (update included)",
+            "value": forms["f64"]["time_to_tol_ms"], "unit": "ms", "higher_is_better": False, "dtype": "f64",
+            "config": {"workload": "torus-800x250-block3", "n_vertices": int(V.shape[0]), "unknowns": int(n),
+                       "launch_classes": classes, "t": 1e-3, "rtol": 1e-9,
+                       "l2": "flushed by a 256 MB write before every timed step"},
+            "setup_s": setup_s, "forms": forms}
+
+
 CONFIGS = {"c1_icosphere4": config_c1, "c2_batch64": config_c2, "c3_icosphere9_mixed": config_c3,
-           "c4_disk400_adjoint": config_c4, "c5_frames655": config_c5}
+           "c4_disk400_adjoint": config_c4, "c5_frames655": config_c5, "f3_block3_torus600k": config_f3}
 WORKLOAD_FLAGS = {"ico2562": "c1_icosphere4", "batch64": "c2_batch64", "ico262": "c3_icosphere9_mixed",
-                  "disk160": "c4_disk400_adjoint", "frames655": "c5_frames655"}
+                  "disk160": "c4_disk400_adjoint", "frames655": "c5_frames655", "block3": "f3_block3_torus600k"}
 
 
 def run_configs(args, local_rank, names):
@@ -929,7 +978,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="40k-vertex torus (profiling captures)")
     ap.add_argument("--workload", default="torus1m", choices=["torus1m"] + sorted(WORKLOAD_FLAGS),
                     help="torus1m: the headline line (with every other workload under \"configs\"); "
-                         "ico2562, batch64, ico262, disk160, frames655: one of those workloads on its own line")
+                         "ico2562, batch64, ico262, disk160, frames655, block3: one of those workloads on its own line")
     ap.add_argument("--headline-only", action="store_true", help="the 1M-vertex torus line without \"configs\"")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",

@@ -243,6 +243,22 @@ def greedy_colouring(S):
     return colour
 
 
+def block_colouring(S, bs):
+    """Colours of a system with bs unknowns per vertex (3|V| systems of Sec. 6;
+    unknown r is component r % bs of vertex r // bs, every level a pattern of
+    bs x bs blocks).  Reading of Alg. 3 for such systems: Alg. 3 colours the
+    vertices (the pattern of the blocks), and vertex colour class C is swept
+    component by component, so unknown (v, c) gets colour bs * C(v) + c."""
+    S = S.tocsr()
+    n = S.shape[0]
+    rows = np.repeat(np.arange(n) // bs, np.diff(S.indptr))
+    Sv = sp.csr_matrix((np.ones(rows.size), (rows, S.indices // bs)), shape=(n // bs, n // bs))
+    Sv.sum_duplicates()
+    Sv.sort_indices()
+    vc = greedy_colouring(Sv).astype(np.int64)
+    return (bs * np.repeat(vc, bs) + np.tile(np.arange(bs), n // bs)).astype(np.int32)
+
+
 def colour_order(colour, reverse=False):
     """Row order of a sweep: colour classes one after another (ascending colour
     ids, or descending when reverse), rows ascending within a class."""
@@ -317,14 +333,15 @@ class Options:
     omega: float = 2.0 / 3.0         # Jacobi damping (the paper gives none; 2/3 is the textbook weight)
 
 
-def build_levels(A0, Ps):
-    """Levels 0..H from A_0 and P_1..P_H: Galerkin products, colourings, the
+def build_levels(A0, Ps, block=1):
+    """Levels 0..H from A_0 and P_1..P_H: Galerkin products, colourings (Alg. 3;
+    with block = 3 the colouring of 3|V| systems, block_colouring), the
     Cholesky factor of A_H."""
     levels = []
     A = A0.tocsr()
     A.sort_indices()
     for P in Ps:
-        col = greedy_colouring(A)
+        col = greedy_colouring(A) if block == 1 else block_colouring(A, block)
         levels.append(Level(A=A, P=P.tocsr(), colour=col, fwd=colour_order(col),
                             rev=colour_order(col, reverse=True)))
         A = galerkin(A, P)

@@ -57,7 +57,7 @@ void drop_graphs(smg_hierarchy* h);
 // ------------------------------------------------------------------ launchers
 template <typename T>
 struct LevelView {
-    const T *sval, *diag, *dinv, *p_w, *pt_w, *rq;
+    const T *sval, *diag, *dinv, *p_w, *pt_w, *rq, *bval, *dblk;
     T *x, *b, *r;
 };
 
@@ -65,11 +65,12 @@ template <typename T>
 LevelView<T> view(DLevel& L);
 template <>
 LevelView<double> view<double>(DLevel& L) {
-    return {L.vals + L.sbase, L.vals, L.dinv, L.p_w, L.pt_w, L.rq_val, L.x, L.b, L.r};
+    return {L.vals + L.sbase, L.vals, L.dinv, L.p_w, L.pt_w, L.rq_val, L.b_val, L.b_dblk, L.x, L.b, L.r};
 }
 template <>
 LevelView<float> view<float>(DLevel& L) {
-    return {L.vals32 + L.sbase, L.vals32, L.dinv32, L.p_w32, L.pt_w32, L.rq_val32, L.x32, L.b32, L.r32};
+    return {L.vals32 + L.sbase, L.vals32, L.dinv32, L.p_w32, L.pt_w32, L.rq_val32, L.b_val32, L.b_dblk32, L.x32, L.b32,
+            L.r32};
 }
 
 // Dispatch on the lanes-per-row of a level (compile-time RR inside CALL).
@@ -92,6 +93,25 @@ int lanes(const DLevel& L) {
 template <typename T, int K>
 void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse, cudaStream_t s, int first = 0) {
     const int R = lanes<T>(L);
+    if (L.bs == 3) {  // 3|V| systems: a vertex class per launch, components in order inside;
+                      // R lanes per vertex
+        const T* bval = v.bval;
+        const T* dblk = v.dblk;
+        for (int cc = first; cc < L.ncolours; cc++) {
+            const int c = reverse ? L.ncolours - 1 - cc : cc;
+            const int s0 = L.b_colour_slice[c], s1 = L.b_colour_slice[c + 1];
+            if (s1 <= s0) continue;
+            const dim3 grid(blocks_for((int64_t)(s1 - s0) * 32 * R)), block(kern::kThreads);
+            const SliceMeta* sl = L.b_slices;
+            const int32_t* bcol = L.b_col;
+            const int64_t nv = L.n / 3;
+            const int rev = reverse ? 1 : 0;
+            SMG_R_SWITCH(R, ck(launch_pdl(kern::gs_block3<T, K, RR>, grid, block, s, sl, s0, s1, bcol, bval, dblk, nv,
+                                            v.dinv, b, x, rev),
+                               "block gs launch"));
+        }
+        return;
+    }
     for (int cc = first; cc < L.ncolours; cc++) {
         const int c = reverse ? L.ncolours - 1 - cc : cc;
         const int s0 = L.colour_slice[c], s1 = L.colour_slice[c + 1];
@@ -190,7 +210,8 @@ size_t tail_bytes(const smg_hierarchy* h, int t, bool single, int K) {
 // First tail level for K right-hand sides: the tuned level, moved down while its
 // shared memory does not fit in one CTA.
 int tail_start(const smg_hierarchy* h, bool single, int K) {
-    if (h->tail_cluster == 0 || h->H == 0 || h->opts.smoother == SMG_SMOOTHER_JACOBI) return h->H;
+    if (h->tail_cluster == 0 || h->H == 0 || h->opts.smoother == SMG_SMOOTHER_JACOBI || h->opts.block_size != 1)
+        return h->H;
     int t = std::min(single ? h->tail32 : h->tail64, h->H);
     while (t < h->H && tail_bytes(h, t, single, K) > kTailSmemMax) t++;
     return t;
@@ -884,6 +905,11 @@ void rec_prep_levels(smg_hierarchy* h, cudaStream_t s) {
         kern::prep_level<<<blocks_for(L.nflat), kern::kThreads, 0, s>>>(L.nflat, L.n, L.vals, L.dinv, L.vals32,
                                                                       L.dinv32);
         kern::copy_f32<<<blocks_for(L.rq_nslots), kern::kThreads, 0, s>>>(L.rq_nslots, L.rq_val, L.rq_val32);
+        if (L.bs == 3) {
+            const int64_t nb = 9 * L.b_nslots, nd = 9 * (L.n / 3);
+            kern::block_gather<<<blocks_for(nb), kern::kThreads, 0, s>>>(nb, L.b_src, L.vals, L.b_val, L.b_val32);
+            kern::block_gather<<<blocks_for(nd), kern::kThreads, 0, s>>>(nd, L.d_src, L.vals, L.b_dblk, L.b_dblk32);
+        }
     }
 }
 
@@ -1057,6 +1083,21 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
         L.colour_slice_dev = upload(h, lp.colour_slice);
         L.colour_row_dev = upload(h, lp.colour_row);
         L.seed_rows = (lp.colour_row.size() > 1 && lp.colour_row[0] == 0) ? lp.colour_row[1] : 0;
+        if (!lp.b_slices.empty()) {  // 3|V| systems: 3 x 3 block layout; a launch class is not one
+                                     // scalar colour, so no colour step is folded into the restriction
+            L.bs = 3;
+            L.seed_rows = 0;
+            L.b_slices = upload(h, lp.b_slices);
+            L.b_colour_slice = lp.b_colour_slice;
+            L.b_col = upload(h, lp.b_col);
+            L.b_src = upload(h, lp.b_src);
+            L.d_src = upload(h, lp.d_src);
+            L.b_nslots = lp.b_nslots;
+            L.b_val = dalloc<double>(h, 9 * lp.b_nslots);
+            L.b_val32 = dalloc<float>(h, 9 * lp.b_nslots);
+            L.b_dblk = dalloc<double>(h, 9 * (L.n / 3));
+            L.b_dblk32 = dalloc<float>(h, 9 * (L.n / 3));
+        }
         for (const SliceMeta& m : lp.slices) L.maxw = std::max(L.maxw, (int)m.width);
         L.dinv = dalloc<double>(h, L.n);
         L.vals32 = dalloc<float>(h, L.nflat);

@@ -61,6 +61,15 @@ struct DLevel {
     int32_t* pt_row = nullptr;
     double* pt_w = nullptr;
     float* pt_w32 = nullptr;
+    // 3|V| systems: the operator in 3 x 3 blocks for the block sweep (layout in
+    // LevelPlan), gathered from the flat values at every update
+    int bs = 1;
+    SliceMeta* b_slices = nullptr;
+    std::vector<int32_t> b_colour_slice;
+    int32_t *b_col = nullptr, *b_src = nullptr, *d_src = nullptr;
+    double *b_val = nullptr, *b_dblk = nullptr;
+    float *b_val32 = nullptr, *b_dblk32 = nullptr;
+    int64_t b_nslots = 0;
     // residual fused with restriction: RQSlice layout over the next level's rows,
     // values [-P^T | Q = P^T A_l] (binary64 and binary32), lanes per row
     RQSlice* rq_slices = nullptr;

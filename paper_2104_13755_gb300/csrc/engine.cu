@@ -600,7 +600,9 @@ __global__ void copy_states(const eng::EMesh* __restrict__ meshes, int nmesh, So
 
 bool engine_supported(const smg_batch* B) {
     for (const smg_hierarchy* h : B->hs)
-        if (h->H < 1 || h->opts.smoother != SMG_SMOOTHER_GS || h->opts.solver != SMG_SOLVER_VCYCLE) return false;
+        if (h->H < 1 || h->opts.smoother != SMG_SMOOTHER_GS || h->opts.solver != SMG_SOLVER_VCYCLE ||
+            h->opts.block_size != 1)
+            return false;
     return true;
 }
 

@@ -46,6 +46,108 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) gs_colour(co
         for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = acc[q] * d;
 }
 
+// 3|V| systems: one launch class (a vertex colour class) of the sweep in 3 x 3
+// blocks.  Unknown (v, c) has colour 3 C(v) + c, so scalar Gauss-Seidel in
+// colour order updates, for each vertex of class C, component 0, then 1, then
+// 2 (reverse sweep: 2, 1, 0), each from the newest values: neighbours of other
+// classes are not updated inside the class, and the vertex's own other
+// components enter through its diagonal block.  R lanes per vertex (32 / R
+// vertices per warp, a slice of 32 vertices over R warps), lane `sub` taking
+// neighbour blocks sub, sub + R, ..., summed over the R lanes by a fixed xor
+// tree; each neighbour block costs one column index and one 24-byte gather of
+// the neighbour's three values.
+template <typename T, int K, int R>
+__global__ void __launch_bounds__(kThreads) gs_block3(const SliceMeta* __restrict__ slices, int s0, int s1,
+                                                      const int32_t* __restrict__ bcol, const T* __restrict__ bval,
+                                                      const T* __restrict__ dblk, int64_t nv,
+                                                      const T* __restrict__ dinv, const T* __restrict__ b,
+                                                      T* __restrict__ x, int reverse) {
+    constexpr int RL = 32 / R;
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int s = s0 + w / R;
+    const int lane = threadIdx.x & 31;
+    if (s >= s1) return;
+    const SliceMeta m = slices[s];
+    const int sub = lane / RL;
+    const int r = (w % R) * RL + (lane % RL);
+    const bool valid = r < m.nrows;
+    const int64_t pv = m.row0 + (valid ? r : 0);
+    T D[9], di[3];
+    if (sub == 0) {
+#pragma unroll
+        for (int q = 0; q < 9; q++) D[q] = ldg(dblk + q * nv + pv);
+#pragma unroll
+        for (int a = 0; a < 3; a++) di[a] = ldg(dinv + 3 * pv + a);
+    }
+    const int32_t* cb = bcol + m.off + r;
+    const T* vb = bval + 9 * (int64_t)m.off + r;
+    int c0 = sub < m.width ? ldg(cb + sub * 32) : 0;
+    pdl_wait();
+    pdl_trigger();
+    T acc[3][K];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[a][q] = (sub == 0) ? b[(3 * pv + a) * K + q] : T(0);
+    for (int k = sub; k < m.width; k += R) {
+        const int c = c0;
+        if (k + R < m.width) c0 = ldg(cb + (k + R) * 32);
+        T xw[3][K];
+#pragma unroll
+        for (int e = 0; e < 3; e++)
+#pragma unroll
+            for (int q = 0; q < K; q++) xw[e][q] = x[(3 * (int64_t)c + e) * K + q];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                const T v = ldg(vb + (9 * k + 3 * a + e) * 32);
+#pragma unroll
+                for (int q = 0; q < K; q++) acc[a][q] -= v * xw[e][q];
+            }
+    }
+#pragma unroll
+    for (int o = 16; o >= RL; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[a][q] += __shfl_xor_sync(0xffffffffu, acc[a][q], o);
+    if (sub != 0 || !valid) return;
+    T xo[3][K], xn[3][K];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int q = 0; q < K; q++) xo[a][q] = x[(3 * pv + a) * K + q];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        if (!reverse) {
+            xn[0][q] = (acc[0][q] - D[1] * xo[1][q] - D[2] * xo[2][q]) * di[0];
+            xn[1][q] = (acc[1][q] - D[3] * xn[0][q] - D[5] * xo[2][q]) * di[1];
+            xn[2][q] = (acc[2][q] - D[6] * xn[0][q] - D[7] * xn[1][q]) * di[2];
+        } else {
+            xn[2][q] = (acc[2][q] - D[6] * xo[0][q] - D[7] * xo[1][q]) * di[2];
+            xn[1][q] = (acc[1][q] - D[3] * xo[0][q] - D[5] * xn[2][q]) * di[1];
+            xn[0][q] = (acc[0][q] - D[1] * xn[1][q] - D[2] * xn[2][q]) * di[0];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int q = 0; q < K; q++) x[(3 * pv + a) * K + q] = xn[a][q];
+}
+
+// Values of the 3 x 3 block layout from the flat values (src -1: zero), binary64
+// and binary32.
+__global__ void block_gather(int64_t m, const int32_t* __restrict__ src, const double* __restrict__ vals,
+                             double* __restrict__ out, float* __restrict__ out32) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    const int32_t k = src[e];
+    const double v = k >= 0 ? vals[k] : 0.0;
+    out[e] = v;
+    out32[e] = (float)v;
+}
+
 // Damped Jacobi update x <- x + omega D^{-1} r after r = b - A x (App.
 // "Ablation Study": the smoother compared with Gauss-Seidel).
 template <typename T, int K>

@@ -344,21 +344,55 @@ int finalize_plan(Plan& p, std::string& err) {
             lv.nflat = n * n;
             continue;
         }
-        lv.ncolours = greedy_colouring(n, lv.rowptr, lv.col, lv.colour);
         std::vector<int32_t> len(n);
         for (int64_t r = 0; r < n; r++) len[r] = (int32_t)(lv.rowptr[r + 1] - lv.rowptr[r] - 1);
         std::iota(lv.perm.begin(), lv.perm.end(), 0);
-        // colour classes one after another; longer rows first inside a class so a
-        // warp's 32 rows have similar lengths (order inside a class does not change
-        // the sweep: no two rows of a class are coupled)
-        std::stable_sort(lv.perm.begin(), lv.perm.end(), [&](int32_t a, int32_t b) {
-            if (lv.colour[a] != lv.colour[b]) return lv.colour[a] < lv.colour[b];
-            return len[a] > len[b];
-        });
+        std::vector<int32_t> cls(n);  // launch class of every row
+        if (bs == 1) {
+            lv.ncolours = greedy_colouring(n, lv.rowptr, lv.col, lv.colour);
+            cls = lv.colour;
+            // colour classes one after another; longer rows first inside a class so a
+            // warp's 32 rows have similar lengths (order inside a class does not change
+            // the sweep: no two rows of a class are coupled)
+            std::stable_sort(lv.perm.begin(), lv.perm.end(), [&](int32_t a, int32_t b) {
+                if (lv.colour[a] != lv.colour[b]) return lv.colour[a] < lv.colour[b];
+                return len[a] > len[b];
+            });
+        } else {
+            // 3|V| systems: Alg. 3 on the vertex pattern; unknown (v, c) has colour
+            // 3 C(v) + c and a vertex class is swept component by component in one
+            // launch, so the launch classes are the vertex classes, with the three
+            // unknowns of a vertex adjacent (longer rows first inside a class)
+            const int64_t nv = n / bs;
+            std::vector<int64_t> vrp(nv + 1, 0);
+            std::vector<int32_t> vcol;
+            for (int64_t v = 0; v < nv; v++) {
+                for (int64_t q = lv.rowptr[bs * v]; q < lv.rowptr[bs * v + 1]; q++) {
+                    const int32_t w = lv.col[q] / bs;
+                    if (vcol.empty() || (int64_t)vcol.size() == vrp[v] || vcol.back() != w) vcol.push_back(w);
+                }
+                vrp[v + 1] = (int64_t)vcol.size();
+            }
+            std::vector<int32_t> vc;
+            lv.ncolours = greedy_colouring(nv, vrp, vcol, vc);
+            lv.colour.resize(n);
+            for (int64_t r = 0; r < n; r++) {
+                lv.colour[r] = bs * vc[r / bs] + (int32_t)(r % bs);
+                cls[r] = vc[r / bs];
+            }
+            std::vector<int32_t> vperm(nv);
+            std::iota(vperm.begin(), vperm.end(), 0);
+            std::stable_sort(vperm.begin(), vperm.end(), [&](int32_t a, int32_t b) {
+                if (vc[a] != vc[b]) return vc[a] < vc[b];
+                return len[bs * a] > len[bs * b];
+            });
+            for (int64_t q = 0; q < nv; q++)
+                for (int c = 0; c < bs; c++) lv.perm[bs * q + c] = bs * vperm[q] + c;
+        }
         for (int64_t q = 0; q < n; q++) lv.iperm[lv.perm[q]] = (int32_t)q;
         const int rows_per_slice = kSlice;
         lv.colour_row.assign(lv.ncolours + 1, 0);
-        for (int64_t r = 0; r < n; r++) lv.colour_row[lv.colour[r] + 1]++;
+        for (int64_t r = 0; r < n; r++) lv.colour_row[cls[r] + 1]++;
         for (int c = 0; c < lv.ncolours; c++) lv.colour_row[c + 1] += lv.colour_row[c];
         lv.slices.clear();
         lv.colour_slice.assign(lv.ncolours + 1, 0);
@@ -421,6 +455,80 @@ int finalize_plan(Plan& p, std::string& err) {
                 }
             }
     }
+
+    // ---- 3|V| systems: 3 x 3 block layout of every sparse level
+    if (bs == 3)
+        for (int l = 0; l < H; l++) {
+            LevelPlan& lv = p.L[l];
+            const int64_t nv = lv.n / 3;
+            std::vector<int32_t> slice_of(lv.n, 0);
+            for (size_t si = 0; si < lv.slices.size(); si++)
+                for (int k = 0; k < lv.slices[si].nrows; k++) slice_of[lv.slices[si].row0 + k] = (int32_t)si;
+            // neighbour vertices of every permuted vertex (ascending) and the flat
+            // index of each scalar entry, keyed by (row component, column)
+            std::vector<std::vector<int32_t>> nbr(nv);
+            lv.d_src.assign(9 * nv, -1);
+            for (int64_t pv = 0; pv < nv; pv++) {
+                for (int a = 0; a < 3; a++) {
+                    const int32_t pr = (int32_t)(3 * pv + a);
+                    lv.d_src[(3 * a + a) * nv + pv] = pr;  // the diagonal entry
+                    const SliceMeta& fs = lv.slices[slice_of[pr]];
+                    const int rl = pr - fs.row0;
+                    for (int k = 0; k < fs.width; k++) {
+                        const int64_t slot = slot_at(fs, rl, k);
+                        const int32_t pc = lv.sell_col[slot];
+                        if (pc == pr) continue;
+                        if (pc / 3 == pv) lv.d_src[(3 * a + pc % 3) * nv + pv] = (int32_t)(lv.sbase + slot);
+                        else nbr[pv].push_back(pc / 3);
+                    }
+                }
+                std::sort(nbr[pv].begin(), nbr[pv].end());
+                nbr[pv].erase(std::unique(nbr[pv].begin(), nbr[pv].end()), nbr[pv].end());
+            }
+            lv.b_slices.clear();
+            lv.b_colour_slice.assign(lv.ncolours + 1, 0);
+            int64_t off = 0;
+            for (int c = 0; c < lv.ncolours; c++) {
+                const int32_t v0 = lv.colour_row[c] / 3, v1 = lv.colour_row[c + 1] / 3;
+                for (int32_t q0 = v0; q0 < v1; q0 += kSlice) {
+                    SliceMeta sm{};
+                    sm.row0 = q0;
+                    sm.nrows = std::min<int32_t>(kSlice, v1 - q0);
+                    for (int r = 0; r < sm.nrows; r++) sm.width = std::max(sm.width, (int32_t)nbr[q0 + r].size());
+                    if (9 * (off + (int64_t)sm.width * kSlice) > (int64_t)INT32_MAX) {
+                        err = "level too large for 32-bit block slots";
+                        return SMG_ERR_INVALID_ARG;
+                    }
+                    sm.off = (int32_t)off;
+                    off += (int64_t)sm.width * kSlice;
+                    lv.b_slices.push_back(sm);
+                }
+                lv.b_colour_slice[c + 1] = (int32_t)lv.b_slices.size();
+            }
+            lv.b_nslots = off;
+            lv.b_col.assign(off, 0);
+            lv.b_src.assign(9 * off, -1);
+            for (const SliceMeta& sm : lv.b_slices)
+                for (int r = 0; r < kSlice; r++) {
+                    const int32_t pv = sm.row0 + (r < sm.nrows ? r : 0);
+                    const int nk = r < sm.nrows ? (int)nbr[pv].size() : 0;
+                    for (int k = 0; k < sm.width; k++) lv.b_col[(int64_t)sm.off + (int64_t)k * kSlice + r] = k < nk ? nbr[pv][k] : pv;
+                    if (r >= sm.nrows) continue;
+                    for (int a = 0; a < 3; a++) {
+                        const int32_t pr = 3 * pv + a;
+                        const SliceMeta& fs = lv.slices[slice_of[pr]];
+                        const int rl = pr - fs.row0;
+                        for (int k = 0; k < fs.width; k++) {
+                            const int64_t slot = slot_at(fs, rl, k);
+                            const int32_t pc = lv.sell_col[slot];
+                            if (pc == pr || pc / 3 == pv) continue;
+                            const int kb = (int)(std::lower_bound(nbr[pv].begin(), nbr[pv].end(), pc / 3) - nbr[pv].begin());
+                            const int64_t at = 9 * (int64_t)sm.off + (int64_t)(9 * kb + 3 * a + pc % 3) * kSlice + r;
+                            lv.b_src[at] = (int32_t)(lv.sbase + slot);
+                        }
+                    }
+                }
+        }
 
     tm.mark("flat -> CSR maps");
     // ---- permuted prolongation, restriction and Galerkin plans

@@ -84,6 +84,18 @@ struct LevelPlan {
     std::vector<int32_t> g_ptr, g_src, g_pw;
     // flat index -> position in the natural CSR pattern (for read-back)
     std::vector<int64_t> flat_to_csr;
+    // 3|V| systems (block size 3): the operator in 3 x 3 blocks for the block
+    // sweep.  Vertex p (permuted) owns rows 3p .. 3p + 2.  Slices of 32 vertices
+    // of one launch class (SliceMeta: row0 = first vertex, nrows = vertices,
+    // width = off-diagonal blocks, off = first block slot); neighbour block k of
+    // local vertex r at slot off + 32 k + r (b_col: neighbour vertex, padding the
+    // vertex itself); its value (a, e) at 9 off + 32 (9 k + 3 a + e) + r, taken
+    // from flat entry b_src[...] (-1: structural zero).  Diagonal blocks:
+    // value (a, e) of vertex p at (3 a + e) nv + p, from d_src.
+    std::vector<SliceMeta> b_slices;
+    std::vector<int32_t> b_colour_slice;
+    std::vector<int32_t> b_col, b_src, d_src;
+    int64_t b_nslots = 0;
 };
 
 struct AssemblyPlan {

@@ -510,7 +510,8 @@ def test_block3_systems_match_oracle(dirichlet):
     (M + t L) (x) I_3; a system with cross-component coupling,
     (M + t L) (x) I_3 + s L (x) J (J the symmetric 3 x 3 tridiagonal ones, s < t /
     sqrt 2 so the sum stays positive definite), goes through update_matrix.
-    Galerkin levels, every cycle and the solves against the oracle."""
+    Galerkin levels, every cycle (the sweep in 3 x 3 blocks, a vertex class per
+    launch) and the solves against the oracle."""
     if dirichlet:
         V, F, known = synth.disk(32, seed=9)
     else:
@@ -529,7 +530,7 @@ def test_block3_systems_match_oracle(dirichlet):
     for name, A in systems:
         A = oracle.on_pattern(S3, A.tocsr())
         Ar, Pr, _, _ = oracle.dirichlet_reduce(A, Ps, np.repeat(known, 3))
-        levels = oracle.build_levels(Ar, Pr)
+        levels = oracle.build_levels(Ar, Pr, block=3)
         if name == "assembled":
             h.update_positions(to_dev(V), t)
         else:
@@ -545,6 +546,7 @@ def test_block3_systems_match_oracle(dirichlet):
             x_or = oracle.vcycle(levels, 0, np.ascontiguousarray(x_or), b, oracle.Options())
             h.vcycle(bd, x_gpu)
             assert rel(x_gpu.cpu().numpy(), x_or) <= CYCLE_TOL, (name, k)
+            assert maxrel(x_gpu.cpu().numpy(), x_or) <= CYCLE_TOL, (name, k)
         xs = spla.splu(Ar.tocsc()).solve(b)
         for kw in (dict(), dict(precision=smg.MIXED), dict(solver=smg.PCG)):
             h.set_options(rtol=1e-10, max_cycles=300, **kw)

@@ -469,6 +469,38 @@ def test_bilaplacian_system_identities():
     assert np.linalg.eigvalsh(A.toarray()).min() > 0
 
 
+def test_block_colouring_sweeps_vertices_component_by_component():
+    """3|V| systems: the colour of unknown (v, c) is 3 C(v) + c with C Alg. 3 on
+    the vertex pattern (pinned by the hand-worked run and the properness
+    tests above), so (i) it is a proper colouring of the block pattern (no two
+    coupled unknowns share a colour), (ii) it restricted to one component is
+    the vertex colouring, and (iii) the sweep in its colour order equals the
+    sweep that visits the vertex classes in order and, inside a class, the
+    components 0, 1, 2 of all its vertices (the triangular solve of the
+    permuted system)."""
+    V, F = synth.perturbed_icosphere(2, seed=4)
+    S = oracle.mesh_pattern(V.shape[0], F)
+    S3 = oracle.block_pattern(S, 3)
+    col = oracle.block_colouring(S3, 3)
+    vc = oracle.greedy_colouring(S)
+    assert np.array_equal(col[0::3], 3 * vc) and np.array_equal(col[2::3], 3 * vc + 2)
+    r, c = S3.nonzero()
+    off = r != c
+    assert not np.any(col[r[off]] == col[c[off]])
+    A = oracle.expand_blocks(oracle.system_matrix(V, F, 1e-2), 3) + \
+        0.001 * sp.kron(oracle.cotan_laplacian(V, F), np.ones((3, 3)))
+    A = oracle.on_pattern(S3, A.tocsr())
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal(A.shape[0])
+    x0 = rng.standard_normal(A.shape[0])
+    x = x0.copy()
+    oracle.gs_sweep(A, x, b, oracle.colour_order(col))
+    order = np.concatenate([3 * np.flatnonzero(vc == k) + comp for k in range(vc.max() + 1) for comp in range(3)])
+    Ap = A.toarray()[np.ix_(order, order)]
+    xp = sla.solve_triangular(np.tril(Ap), b[order] - np.triu(Ap, 1) @ x0[order], lower=True)
+    assert np.abs(x[order] - xp).max() < 1e-13 * np.abs(xp).max()
+
+
 def test_block_expansion_identities():
     """X (x) I_3: (A (x) I)(u (x) e_k) = (A u) (x) e_k, and a Galerkin product of
     expanded operators is the expansion of the vertex Galerkin product."""

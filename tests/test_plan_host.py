@@ -187,8 +187,9 @@ def test_two_ring_plan_patterns_and_colouring_match_oracle(dirichlet):
 @pytest.mark.parametrize("dirichlet", [False, True])
 def test_block3_plan_patterns_and_colouring_match_oracle(dirichlet):
     """block_size = 3 (3|V| systems, Sec. 6): level 0 is the vertex pattern in
-    3 x 3 blocks over the unknowns, P is P (x) I_3, and every coarse pattern and
-    colouring follows from them as for scalar systems."""
+    3 x 3 blocks over the unknowns, P is P (x) I_3, every coarse pattern follows
+    from them as for scalar systems, and every colouring is Alg. 3 on the
+    vertex pattern with the components in order (oracle.block_colouring)."""
     if dirichlet:
         V, F, known = synth.disk(20, seed=2)
     else:
@@ -207,5 +208,5 @@ def test_block3_plan_patterns_and_colouring_match_oracle(dirichlet):
         Sp.sort_indices()
         assert np.array_equal(rp, Sp.indptr) and np.array_equal(ci, Sp.indices), l
         if l < plan.num_levels - 1:
-            assert np.array_equal(plan.colouring(l), oracle.greedy_colouring(Sp))
+            assert np.array_equal(plan.colouring(l), oracle.block_colouring(Sp, 3))
             S = oracle.galerkin_pattern(Sp, Ps[l])
