@@ -387,6 +387,11 @@ __device__ int run_unit(const EMesh& M, const Phase& ph, int u, int lane) {
     return -1;
 }
 
+// Acquire-release fence at device scope: orders this thread's (and, through
+// the warp barriers around it, its warp's) memory operations against the
+// scheduling atomics; lighter than a sequentially consistent fence.
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ long long globaltimer() {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -425,7 +430,7 @@ __global__ void __launch_bounds__(256, MINB) engine(const EMesh* __restrict__ me
                     got = 1;
                     p = p2;
                     u = u2;
-                    __threadfence();  // acquire: the phase's inputs, published before the ticket
+                    fence_acq_rel();  // acquire: the phase's inputs, published before the ticket
                 }
             }
             if (!got && !moved && !stop) {
@@ -451,15 +456,15 @@ __global__ void __launch_bounds__(256, MINB) engine(const EMesh* __restrict__ me
         const EMesh& M = meshes[m];
         const Phase ph = M.prog[p];
         const int next = run_unit<K>(M, ph, u, lane);
-        __threadfence();  // release: this unit's results before its completion count
+        fence_acq_rel();  // release: this unit's results before its completion count
         __syncwarp();
         if (lane == 0) {
             const unsigned int d = atomicAdd(&ctl[m].done, 1u);
             if (d + 1 == (unsigned int)ph.units) {  // last unit: advance the mesh
-                __threadfence();
+                fence_acq_rel();
                 const int np = next >= 0 ? next : p + 1;
                 atomicExch(&ctl[m].done, 0u);
-                __threadfence();
+                fence_acq_rel();
                 atomicExch(&ctl[m].ticket, (unsigned long long)np << 32);
                 if (np >= M.nphase) {
                     M.trace[1 + m] = globaltimer();
