@@ -409,29 +409,42 @@ __global__ void __launch_bounds__(256, MINB) engine(const EMesh* __restrict__ me
     // unknowns, so polling is spread over the meshes' control words); when
     // that mesh is done it moves on to the next mesh that is not
     int m = home[gw];
+    int visit = (m + 1 + gw % max(nmesh - 1, 1)) % nmesh;  // mesh to help while the own one has nothing to hand out
     long long idle_since = 0;
     int backoff = 32;
     for (;;) {
-        int p = 0, u = 0, got = 0, moved = 0, stop = 0;
+        int p = 0, u = 0, got = 0, moved = 0, stop = 0, cur = m;
         if (lane == 0) {
-            const EMesh& M = meshes[m];
-            const unsigned long long tw = *(volatile unsigned long long*)&ctl[m].ticket;
-            const int pp = (int)(tw >> 32), uu = (int)(tw & 0xffffffffu);
-            if (pp >= M.nphase) {  // this mesh is done
+            // take a unit of mesh c if its current phase has one left
+            auto take = [&](int c) {
+                const EMesh& M = meshes[c];
+                const unsigned long long tw = *(volatile unsigned long long*)&ctl[c].ticket;
+                const int pp = (int)(tw >> 32), uu = (int)(tw & 0xffffffffu);
+                if (pp >= M.nphase || uu >= M.prog[pp].units) return pp >= M.nphase ? 2 : 0;
+                const unsigned long long old = atomicAdd(&ctl[c].ticket, 1ull);
+                const int p2 = (int)(old >> 32), u2 = (int)(old & 0xffffffffu);
+                if (p2 < M.nphase && u2 < M.prog[p2].units) {
+                    p = p2;
+                    u = u2;
+                    cur = c;
+                    fence_acq_rel();  // acquire: the phase's inputs, published before the ticket
+                    return 1;
+                }
+                return 0;
+            };
+            const int r = take(m);
+            if (r == 1) {
+                got = 1;
+            } else if (r == 2) {  // this mesh is done
                 if (*(volatile int*)finished >= nmesh || *(volatile int*)err) stop = 1;
                 else {
                     m = (m + 1) % nmesh;
                     moved = 1;
                 }
-            } else if (uu < M.prog[pp].units) {
-                const unsigned long long old = atomicAdd(&ctl[m].ticket, 1ull);
-                const int p2 = (int)(old >> 32), u2 = (int)(old & 0xffffffffu);
-                if (p2 < M.nphase && u2 < M.prog[p2].units) {
-                    got = 1;
-                    p = p2;
-                    u = u2;
-                    fence_acq_rel();  // acquire: the phase's inputs, published before the ticket
-                }
+            } else if (nmesh > 1) {  // help another mesh for one unit
+                if (visit == m) visit = (visit + 1) % nmesh;
+                got = take(visit) == 1;
+                visit = (visit + 1) % nmesh;
             }
             if (!got && !moved && !stop) {
                 if (*(volatile int*)err) stop = 1;
@@ -442,6 +455,7 @@ __global__ void __launch_bounds__(256, MINB) engine(const EMesh* __restrict__ me
         }
         if (__shfl_sync(0xffffffffu, stop, 0)) return;
         m = __shfl_sync(0xffffffffu, m, 0);
+        cur = __shfl_sync(0xffffffffu, cur, 0);
         if (__shfl_sync(0xffffffffu, moved, 0)) continue;
         if (!__shfl_sync(0xffffffffu, got, 0)) {
             __nanosleep(backoff);
@@ -453,21 +467,21 @@ __global__ void __launch_bounds__(256, MINB) engine(const EMesh* __restrict__ me
         __syncwarp();  // order the lanes' reads after lane 0's acquire
         idle_since = 0;
         backoff = 32;
-        const EMesh& M = meshes[m];
+        const EMesh& M = meshes[cur];
         const Phase ph = M.prog[p];
         const int next = run_unit<K>(M, ph, u, lane);
         fence_acq_rel();  // release: this unit's results before its completion count
         __syncwarp();
         if (lane == 0) {
-            const unsigned int d = atomicAdd(&ctl[m].done, 1u);
+            const unsigned int d = atomicAdd(&ctl[cur].done, 1u);
             if (d + 1 == (unsigned int)ph.units) {  // last unit: advance the mesh
                 fence_acq_rel();
                 const int np = next >= 0 ? next : p + 1;
-                atomicExch(&ctl[m].done, 0u);
+                atomicExch(&ctl[cur].done, 0u);
                 fence_acq_rel();
-                atomicExch(&ctl[m].ticket, (unsigned long long)np << 32);
+                atomicExch(&ctl[cur].ticket, (unsigned long long)np << 32);
                 if (np >= M.nphase) {
-                    M.trace[1 + m] = globaltimer();
+                    M.trace[1 + cur] = globaltimer();
                     atomicAdd(finished, 1);
                 }
             }
