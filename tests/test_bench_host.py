@@ -27,3 +27,12 @@ def test_sweep_bytes_formula():
     n, z = 1000, 7000
     assert bench.sweep_bytes(n, z) == z * 12 + 4 * (n + 1) + 3 * 8 * n
     assert bench.sweep_bytes(n, z, s=4, k=2) == z * 8 + 4 * (n + 1) + 3 * 4 * 2 * n
+
+
+def test_captured_cycle_traffic_follows_the_sources(monkeypatch):
+    """The DRAM traffic of one captured cycle is reported only while the
+    kernel and layout sources hash to the captured ones."""
+    got = bench.captured_cycle_traffic()
+    assert got is None or got == bench.CYCLE_TRAFFIC["bytes_per_cycle"]
+    monkeypatch.setattr(bench, "CYCLE_TRAFFIC", dict(bench.CYCLE_TRAFFIC, sha256="0" * 64))
+    assert bench.captured_cycle_traffic() is None
