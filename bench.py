@@ -482,6 +482,8 @@ def run_ours(args, w, rank, world, local_rank):
                    "colours": [plan.level_info(l)[2] for l in range(plan.num_levels)],
                    "lanes_per_row_f64": [h.level_config(l)[0] for l in range(plan.num_levels - 1)],
                    "lanes_per_row_f32": [h.level_config(l)[1] for l in range(plan.num_levels - 1)],
+                   "staged_sweep_f64": [h.level_staged(l)[0] for l in range(plan.num_levels - 1)],
+                   "staged_sweep_f32": [h.level_staged(l)[1] for l in range(plan.num_levels - 1)],
                    "restriction": [dict(zip(("q_entries", "pt_entries", "slots", "lanes_f64", "lanes_f32"),
                                             h.level_restriction(l))) for l in range(plan.num_levels - 1)],
                    "cluster_tail_from_level": {"f64": h.cycle_config()[1], "f32": h.cycle_config()[2],
@@ -507,7 +509,9 @@ def run_ours(args, w, rank, world, local_rank):
                                        "of one plain cycle graph",
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_cycle": cb64, "cycle_us": cyc64_ms * 1e3},
-        "roofline_sweep_l0": {"kernel": "gs_colour<double,1> level-0 sweep (all colour launches)", "bound": "hbm",
+        "roofline_sweep_l0": {"kernel": ("gs_colour_bulk<double,1,8> (entries staged by TMA)" if h.level_staged(0)[0]
+                                         else "gs_colour<double,1,%d>" % h.level_config(0)[0])
+                              + " level-0 sweep (all colour launches)", "bound": "hbm",
                               "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                               "traffic": captured_traffic(), "traffic_source": "ncu dram__bytes_read.sum + "
                               "dram__bytes_write.sum per sweep", "bytes_per_sweep": sb},
@@ -990,6 +994,9 @@ def main():
     ap.add_argument("--lanes-f32", default=None, help="the same for the binary32 kernels (with --lanes)")
     ap.add_argument("--rq-lanes", default=None, help="lanes per row of the fused restriction, per level (with --lanes)")
     ap.add_argument("--rq-lanes-f32", default=None, help="the same for binary32 (with --lanes)")
+    ap.add_argument("--staged", default=None,
+                    help="per level 1 = one lane per row with TMA-staged entries, e.g. 1,0,0,0,0 (with --lanes)")
+    ap.add_argument("--staged-f32", default=None, help="the same for binary32 (with --lanes)")
     ap.add_argument("--tail", default=None, help="first level of the cluster tail (skips its tuning; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -998,7 +1005,8 @@ def main():
     if args.lanes:
         os.environ["SMG_LANES_PER_ROW"] = args.lanes
         for flag, var in ((args.lanes_f32, "SMG_LANES_PER_ROW_F32"), (args.rq_lanes, "SMG_RQ_LANES"),
-                          (args.rq_lanes_f32, "SMG_RQ_LANES_F32")):
+                          (args.rq_lanes_f32, "SMG_RQ_LANES_F32"), (args.staged, "SMG_STAGED_GS"),
+                          (args.staged_f32, "SMG_STAGED_GS_F32")):
             if flag:
                 os.environ[var] = flag
     if args.tail:

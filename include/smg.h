@@ -305,6 +305,14 @@ int  smg_run_stage(smg_hierarchy *h, int stage, int level, int nrhs, int precisi
  * kernels, out[1] of the binary32 kernels, out[2] colour classes, out[3] slices. */
 int  smg_level_config(const smg_hierarchy *h, int level, int32_t out[4]);
 
+/* Form of the Gauss-Seidel colour steps of a level (App. "Multi-Color Gauss
+ * Seidel"): out[0] / out[1] = 1 when the binary64 / binary32 sweep runs one
+ * lane per row with each warp's slice of matrix entries (8 per row) staged in
+ * shared memory by bulk (TMA) copies, 0 for the register-prefetching kernel
+ * with the lanes per row of smg_level_config (the autotuner times both).
+ * level in 0..H. */
+int  smg_level_staged(const smg_hierarchy *h, int level, int32_t out[2]);
+
 /* Residual fused with restriction from level l to l + 1 (Alg. 2 "compute
  * residual", "restrict residual" as one product b_{l+1} = P^T b_l - Q x_l with
  * Q = P^T A_l, the first stage of the Galerkin product of Eq. gca): out[0]

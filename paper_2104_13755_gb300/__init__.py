@@ -91,6 +91,7 @@ def _load():
         "smg_run_stage": (I32, [P, I32, I32, I32, I32, I32, P]),
         "smg_level_config": (I32, [P, I32, P]),
         "smg_level_restriction": (I32, [P, I32, P]),
+        "smg_level_staged": (I32, [P, I32, P]),
         "smg_cycle_config": (I32, [P, P]),
         "smg_device_bytes": (I64, [P]),
         "smg_residual_norms_noalloc": (I32, [I64, P, P, P, P, P, I32, P, P]),
@@ -401,6 +402,14 @@ class Hierarchy:
         binary32) of the fused residual-restriction operator from `level` to the next."""
         out = (ctypes.c_int64 * 5)()
         _check(lib.smg_level_restriction(self._h, level, out), "smg_level_restriction")
+        return tuple(out)
+
+    def level_staged(self, level):
+        """(binary64, binary32): 1 where the level's sweep runs one lane per row with
+        its matrix entries staged in shared memory by bulk copies, 0 for the
+        register-prefetching kernel."""
+        out = (ctypes.c_int32 * 2)()
+        _check(lib.smg_level_staged(self._h, level, out), "smg_level_staged")
         return tuple(out)
 
     def cycle_config(self):

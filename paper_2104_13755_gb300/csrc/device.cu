@@ -90,6 +90,8 @@ int lanes(const DLevel& L) {
     return sizeof(T) == 4 ? L.R32 : L.R;
 }
 
+constexpr int kBulkEntries = 8;  // entries per row staged by gs_colour_bulk (wider rows read the rest directly)
+
 template <typename T, int K>
 void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse, cudaStream_t s, int first = 0) {
     const int R = lanes<T>(L);
@@ -112,6 +114,7 @@ void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse,
         }
         return;
     }
+    const bool bulk = R == 1 && (sizeof(T) == 4 ? L.bulk32 : L.bulk);
     for (int cc = first; cc < L.ncolours; cc++) {
         const int c = reverse ? L.ncolours - 1 - cc : cc;
         const int s0 = L.colour_slice[c], s1 = L.colour_slice[c + 1];
@@ -119,6 +122,13 @@ void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse,
         const dim3 grid(blocks_for((int64_t)(s1 - s0) * 32 * R)), block(kern::kThreads);
         const SliceMeta* sl = L.slices;
         const int32_t* col = L.sell_col;
+        if (bulk) {
+            constexpr int WC = kBulkEntries;
+            ck(launch_pdl_smem(kern::gs_colour_bulk<T, K, WC>, grid, block, (size_t)kern::BulkCfg<T, K, WC>::block_bytes,
+                               s, sl, s0, s1, col, v.sval, v.dinv, b, x, (int*)L.bulk_err),
+               "staged gs launch");
+            continue;
+        }
         SMG_R_SWITCH(R, ck(launch_pdl(kern::gs_colour<T, K, RR>, grid, block, s, sl, s0, s1, col, v.sval, v.dinv,
                                         b, x), "gs launch"));
     }
@@ -533,6 +543,20 @@ int env_lanes(const char* name, int level) {
     return (r == 1 || r == 2 || r == 4 || r == 8 || r == 16) ? r : 0;
 }
 
+// Per-level 0/1 list (comma-separated) from the environment: -1 when unset or
+// shorter than level + 1 entries.
+int env_flag(const char* name, int level) {
+    const char* env = std::getenv(name);
+    if (!env) return -1;
+    const char* p = env;
+    for (int q = 0; q < level; q++) {
+        p = std::strchr(p, ',');
+        if (!p) return -1;
+        p++;
+    }
+    return *p == '1' ? 1 : (*p == '0' ? 0 : -1);
+}
+
 // With SMG_LANES_PER_ROW set (a measurement aid: profilers serialise launches,
 // which changes what the timing would pick), the lanes of the smoother
 // (SMG_LANES_PER_ROW, SMG_LANES_PER_ROW_F32) and of the fused restriction
@@ -554,20 +578,33 @@ void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
         int R = 1;
         while (R < 16 && (p90 + R - 1) / R > 8) R *= 2;
         L.R = L.R32 = R;
+        L.bulk = L.bulk32 = false;
+        L.bulk_err = &h->state->bulk_err;
         if (env) {
             if (int r = env_lanes("SMG_LANES_PER_ROW", l)) L.R = L.R32 = r;
             if (int r = env_lanes("SMG_LANES_PER_ROW_F32", l)) L.R32 = r;
             if (int r = env_lanes("SMG_RQ_LANES", l)) L.Rq = L.Rq32 = r;
             if (int r = env_lanes("SMG_RQ_LANES_F32", l)) L.Rq32 = r;
+            L.bulk = L.R == 1 && env_flag("SMG_STAGED_GS", l) == 1;
+            L.bulk32 = L.R32 == 1 && env_flag("SMG_STAGED_GS_F32", l) == 1;
             continue;
         }
         if (!tune) continue;
         for (int prec = 0; prec < 2; prec++) {
             float best = 1e30f;
             int bestR = R;
-            for (int cand : {1, 2, 4, 8, 16}) {
-                if (prec == 0) L.R = cand;
-                else L.R32 = cand;
+            bool bestBulk = false;
+            // one lane per row (register-prefetching, then staged), then 2..16 lanes per row
+            for (int cand = 0; cand < 6; cand++) {
+                const int rc = cand <= 1 ? 1 : 1 << (cand - 1);
+                const bool form = cand == 1;
+                if (prec == 0) {
+                    L.R = rc;
+                    L.bulk = form;
+                } else {
+                    L.R32 = rc;
+                    L.bulk32 = form;
+                }
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; rep++) {
                     if (prec == 0) {
@@ -588,15 +625,21 @@ void choose_lanes(smg_hierarchy* h, const Plan& P, bool tune) {
                     ms = rep == 0 ? t : std::min(ms, t);
                 }
                 if (std::getenv("SMG_TRACE_TUNE"))
-                    std::fprintf(stderr, "[smg tune] level %d %s sweep, %2d lanes/row: %.1f us\n", l,
-                                 prec ? "f32" : "f64", cand, ms * 250.0f);
-                if (ms < best * 0.97f) {  // a larger R must win clearly
+                    std::fprintf(stderr, "[smg tune] level %d %s sweep, %2d lanes/row%s: %.1f us\n", l,
+                                 prec ? "f32" : "f64", rc, form ? " (staged)" : "", ms * 250.0f);
+                if (ms < best * 0.97f) {  // a later candidate must win clearly
                     best = ms;
-                    bestR = cand;
+                    bestR = rc;
+                    bestBulk = form;
                 }
             }
-            if (prec == 0) L.R = bestR;
-            else L.R32 = bestR;
+            if (prec == 0) {
+                L.R = bestR;
+                L.bulk = bestBulk;
+            } else {
+                L.R32 = bestR;
+                L.bulk32 = bestBulk;
+            }
         }
         // lanes per row of the fused residual-restriction kernel, the same way
         DLevel& N = h->L[l + 1];
@@ -1456,6 +1499,7 @@ int smg_solve_result(smg_hierarchy* h, smg_info* info) {
     }
     if (ss.chol_bad) return fail("coarsest operator is not positive definite", SMG_ERR_NOT_SPD);
     if (ss.tail_err) return fail("cluster tail: a step barrier wait timed out", SMG_ERR_TIMEOUT);
+    if (ss.bulk_err) return fail("Gauss-Seidel: a bulk copy of matrix entries did not complete", SMG_ERR_TIMEOUT);
     if (ss.status == SMG_ERR_NOT_CONVERGED) return fail("not converged within max_cycles", ss.status);
     if (ss.status == SMG_ERR_DIVERGED) return fail("residual became non-finite", ss.status);
     return SMG_OK;
@@ -1596,6 +1640,14 @@ int smg_level_config(const smg_hierarchy* h, int level, int32_t out[4]) {
     out[1] = L.R32;
     out[2] = L.ncolours;
     out[3] = L.nslices;
+    return SMG_OK;
+}
+
+int smg_level_staged(const smg_hierarchy* h, int level, int32_t out[2]) {
+    if (!h || !out || level < 0 || level > h->H) return fail("invalid argument", SMG_ERR_INVALID_ARG);
+    const DLevel& L = h->L[level];
+    out[0] = L.bulk ? 1 : 0;
+    out[1] = L.bulk32 ? 1 : 0;
     return SMG_OK;
 }
 

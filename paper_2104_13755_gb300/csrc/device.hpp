@@ -24,6 +24,7 @@ struct SolveState {
     int32_t status;          // SMG_OK / SMG_ERR_NOT_CONVERGED / SMG_ERR_DIVERGED / -1 running
     int32_t chol_bad;        // nonzero: a coarsest pivot was not positive
     int32_t tail_err;        // nonzero: a cluster-tail step barrier wait timed out
+    int32_t bulk_err;        // nonzero: a staged Gauss-Seidel launch's bulk copy did not complete
     double cg_rho[2][kMaxRhs];  // conjugate gradients: r . z of the last two iterations (slot = iteration & 1)
 };
 
@@ -33,6 +34,8 @@ struct DLevel {
     int ncolours = 0, nslices = 0;
     int R = 1;    // lanes per row of the binary64 kernels
     int R32 = 1;  // lanes per row of the binary32 kernels
+    bool bulk = false, bulk32 = false;  // one lane per row with TMA-staged entries (gs_colour_bulk)
+    int32_t* bulk_err = nullptr;        // SolveState::bulk_err of the hierarchy
     int32_t* colour_slice_dev = nullptr;
     int32_t* colour_row_dev = nullptr;
     int maxw = 0;  // widest slice (off-diagonal entries per row)
@@ -223,6 +226,23 @@ inline cudaError_t launch_cluster_pdl(void (*kernel)(Params...), int cluster, di
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// launch_pdl (below) with `smem` bytes of dynamic shared memory.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl_smem(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                   Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

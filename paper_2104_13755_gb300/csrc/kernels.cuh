@@ -15,6 +15,41 @@ namespace smg {
 namespace kern {
 
 // ---------------------------------------------------------------------------
+// mbarrier and bulk-copy (TMA) primitives on shared::cta addresses.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// This thread's arrival on the barrier, announcing `bytes` of asynchronous copies.
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global memory into this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Wait (CTA scope, acquire) for phase `parity` of the barrier, at most `limit`
+// polls; false when the polls ran out.
+__device__ __forceinline__ bool mbar_wait_cta(uint32_t bar, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr int kBulkWaitPolls = 1 << 22;  // far beyond any copy of a few KB; each poll may suspend the thread
+
+// ---------------------------------------------------------------------------
 // Multicolour Gauss-Seidel (App. "Multi-Color Gauss Seidel"): one colour class,
 // x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii for every row i of the class.
 // No row of a class is coupled to another row of the same class, so the rows
@@ -42,6 +77,87 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) gs_colour(co
     for (int q = 0; q < K; q++) bv[q] = b[(int64_t)row * K + q];
     rs.dot_from(m, col, sval, x, bv, acc);  // b_i - sum_{j != i} a_ij x_j
     if (valid && rs.sub == 0)
+#pragma unroll
+        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = acc[q] * d;
+}
+
+// One lane per row with the slice's entries staged by TMA: the form of
+// gs_colour<T, K, 1> for the finest level, where a colour class is ~10^5-10^6
+// short rows.  Each warp's slice of column indices and values (its first WC
+// entries per row) comes into shared memory by two bulk copies that complete
+// on a warp-private mbarrier, issued before the dependency wait.  No entry is
+// held in registers across the wait, so eight 256-thread blocks stay resident
+// per SM and a ~250k-row class is in flight in one wave, where the
+// register-prefetching kernel (five blocks per SM) runs it in two.  The
+// arithmetic is that of gs_colour<T, K, 1>: one FMA chain from b in slot order,
+// then the product with the reciprocal diagonal.  Entries past WC (rare wide
+// rows) are read from global memory.  A copy that never completes leaves the
+// warp after kBulkWaitPolls polls with *err set and its rows unchanged.
+template <typename T, int K, int WC>
+struct BulkCfg {
+    static constexpr int col_bytes = WC * 32 * 4;
+    static constexpr int warp_bytes = WC * 32 * (4 + (int)sizeof(T));  // indices, then values
+    static constexpr int block_bytes = kWarps * warp_bytes + kWarps * 8;  // entries, then one mbarrier per warp
+    static constexpr int min_blocks = K == 1 ? 8 : (K == 2 ? 4 : 2);    // 32 / 64 / 128 registers per thread
+};
+template <typename T, int K, int WC>
+__global__ void __launch_bounds__(kThreads, (BulkCfg<T, K, WC>::min_blocks))
+    gs_colour_bulk(const SliceMeta* __restrict__ slices, int s0, int s1, const int32_t* __restrict__ col,
+                   const T* __restrict__ sval, const T* __restrict__ dinv, const T* __restrict__ b,
+                   T* __restrict__ x, int* __restrict__ err) {
+    using C = BulkCfg<T, K, WC>;
+    extern __shared__ __align__(16) unsigned char bulk_smem[];
+    const int wib = threadIdx.x >> 5;
+    const int s = s0 + (int)blockIdx.x * kWarps + wib;
+    const int lane = threadIdx.x & 31;
+    if (s >= s1) return;
+    const SliceMeta m = slices[s];
+    const int32_t* scol = reinterpret_cast<const int32_t*>(bulk_smem + wib * C::warp_bytes);
+    const T* sv = reinterpret_cast<const T*>(bulk_smem + wib * C::warp_bytes + C::col_bytes);
+    const uint32_t bar = smem_u32(bulk_smem) + (uint32_t)(kWarps * C::warp_bytes + 8 * wib);
+    const int Wc = m.width < WC ? m.width : WC;
+    if (lane == 0 && Wc > 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect(bar, (uint32_t)(Wc * 32 * (4 + (int)sizeof(T))));
+        bulk_g2s(smem_u32(scol), col + m.off, (uint32_t)(Wc * 32 * 4), bar);
+        bulk_g2s(smem_u32(sv), sval + m.off, (uint32_t)(Wc * 32 * (int)sizeof(T)), bar);
+    }
+    __syncwarp();
+    const bool valid = lane < m.nrows;
+    const int row = m.row0 + (valid ? lane : 0);
+    const T d = dinv[row];
+    pdl_wait();
+    pdl_trigger();
+    T acc[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) acc[q] = b[(int64_t)row * K + q];
+    if (Wc > 0 && !mbar_wait_cta(bar, 0, kBulkWaitPolls)) {
+        atomicExch(err, 1);
+        mbar_wait_cta(bar, 0, kBulkWaitPolls);  // the copies land before the block's shared memory is released
+        return;
+    }
+    T xv[WC][K];
+#pragma unroll
+    for (int u = 0; u < WC; u++)
+        if (u < Wc) {
+            const int c = scol[u * 32 + lane];
+#pragma unroll
+            for (int q = 0; q < K; q++) xv[u][q] = ldg(x + (int64_t)c * K + q);
+        }
+#pragma unroll
+    for (int u = 0; u < WC; u++)
+        if (u < Wc) {
+            const T v = sv[u * 32 + lane];
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[q] -= v * xv[u][q];
+        }
+    for (int k = WC; k < m.width; k++) {  // rows wider than the staged part
+        const int cc = ldg(col + m.off + k * 32 + lane);
+        const T vv = ldg(sval + m.off + k * 32 + lane);
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] -= vv * ldg(x + (int64_t)cc * K + q);
+    }
+    if (valid)
 #pragma unroll
         for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = acc[q] * d;
 }

@@ -230,11 +230,7 @@ struct LevelCtx {
     __device__ __forceinline__ int unit(int i, int f) const { return lds_i(tab + 4u * (3 + 2 * nc + 6 * i + f)); }
 };
 
-// mbarrier and bulk-copy helpers (shared::cta addresses).
-__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
+// mbarrier helpers (shared::cta addresses; mbar_init is in kernels.cuh).
 // A value into shared::cluster address a, counted on the mbarrier at cluster
 // address bar (in the CTA that owns a) as sizeof(value) completed bytes.
 __device__ __forceinline__ void st_async(uint32_t a, double v, uint32_t bar) {
@@ -284,10 +280,9 @@ struct StepBars {
 };
 
 // Copy this CTA's slice table into shared memory, and its slices' matrix
-// entries too when the level is staged (bulk copies completing on the CTA's
-// mbarrier, one per slice and array); gather b of its slices' rows into the
-// local copy.  CTA-local, ends with __syncthreads.  `phase` counts the uses of
-// the mbarrier.
+// entries too when the level is staged (4-16 byte asynchronous copies, all in
+// flight together); gather b of its slices' rows into the local copy.
+// CTA-local, ends with __syncthreads.
 template <typename T, int K>
 __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const Dist& D) {
     const TailLevel<T>& L = *Lp;

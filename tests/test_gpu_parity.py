@@ -266,6 +266,62 @@ def test_cluster_tail_and_launch_paths_match_oracle(tail, nrhs, monkeypatch):
     c.h.close()
 
 
+def _staged_env(monkeypatch, on):
+    """Every level one lane per row, its sweep staged by TMA (on) or not, no cluster tail."""
+    monkeypatch.setenv("SMG_TAIL_LEVEL", "99")
+    monkeypatch.setenv("SMG_LANES_PER_ROW", ",".join(["1"] * 12))
+    flags = ",".join([("1" if on else "0")] * 12)
+    monkeypatch.setenv("SMG_STAGED_GS", flags)
+    monkeypatch.setenv("SMG_STAGED_GS_F32", flags)
+
+
+@pytest.mark.parametrize("mesh", ["sphere", "disk", "torus"])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4])
+def test_staged_sweep_matches_oracle_and_register_kernel(mesh, nrhs, monkeypatch):
+    """The sweep with each warp's slice of entries brought into shared memory by
+    bulk copies (gs_colour_bulk) on every level, coarse rows wider than the
+    staged part taking the rest from global memory: each binary64 cycle iterate
+    matches the oracle and is bitwise that of the register-prefetching kernel
+    with one lane per row (the same FMA chain); the mixed-precision solve too."""
+    if mesh == "sphere":
+        V, F = synth.perturbed_geodesic_sphere(14, seed=7)  # valences 5 to 7
+        mask = None
+    elif mesh == "torus":
+        V, F = synth.torus(120, 40, seed=2)  # 1,200-row colour classes: several blocks per launch
+        mask = None
+    else:
+        V, F, mask = synth.disk(40, seed=5)
+    _staged_env(monkeypatch, True)
+    c = Case(V, F, 1e-2, mask=mask, min_coarse=100)
+    H = c.h.cycle_config()[0]
+    assert H >= 2 and all(c.h.level_staged(l) == (1, 1) for l in range(H))
+    assert max(c.plan.level_info(l)[1] / c.plan.level_info(l)[0] for l in range(1, H)) > 9  # wide coarse rows
+    _staged_env(monkeypatch, False)
+    ref = smg.Hierarchy(c.plan)
+    ref.update_positions(c.Vd, 1e-2)
+    assert all(ref.level_staged(l) == (0, 0) and ref.level_config(l)[:2] == (1, 1) for l in range(H))
+    b = synth.uniform_rhs(c.n, nrhs=nrhs, seed=21)
+    bd = to_dev(b)
+    x_or = np.zeros_like(b)
+    xs, xr = to_dev(x_or.copy()), to_dev(x_or.copy())
+    for k in range(3):
+        x_or = oracle.vcycle(c.levels, 0, np.ascontiguousarray(x_or), b, oracle.Options())
+        c.h.vcycle(bd, xs)
+        ref.vcycle(bd, xr)
+        xg = xs.cpu().numpy()
+        assert maxrel(xg, x_or) <= CYCLE_TOL, k
+        assert np.array_equal(xg, xr.cpu().numpy()), k
+    for h in (c.h, ref):
+        h.set_options(rtol=1e-10, precision=smg.MIXED)
+    x1, i1 = c.h.solve(bd)
+    x2, i2 = ref.solve(bd)
+    assert i1["return"] == 0 and i1["cycles"] == i2["cycles"]
+    assert torch.equal(x1, x2)
+    assert oracle.rel_residual(c.A, x1.cpu().numpy(), b) <= 1e-10
+    c.h.close()
+    ref.close()
+
+
 @pytest.fixture(scope="module")
 def batch_cases():
     """Uneven meshes (spheres, tori, a Dirichlet disk) for the batched form."""
