@@ -6,6 +6,10 @@
 //
 // Blocked right-looking algorithms with 32 x 32 tiles; the matrix is padded to
 // a multiple of 32 with an identity block.
+#include <algorithm>
+#include <stdexcept>
+#include <string>
+
 #include "device.hpp"
 
 namespace smg {
@@ -32,7 +36,35 @@ __global__ void k_pad_copy(const double* __restrict__ A, int64_t n, double* __re
 // warp applies pivot k to its columns right of k + 1 (lower triangle).  The
 // owner catches up on pivot k in step k + 1, so the published columns rotate
 // over three buffers and one barrier per pivot suffices.
+// Reciprocal square root on the pivot chain (a positive binary64 pivot): a
+// binary32 estimate y0 (the leading bits of a moved into a float by integer
+// operations, one rsqrtf), then one second-order correction from the binomial
+// series of (1 - e)^(-1/2): y = y0 (1 + e/2 + 3 e^2 / 8) with e = 1 - a y0^2,
+// whose truncation error (~5 e^3 / 16, e < 2^-20) is far below binary64
+// rounding.  Four dependent binary64 operations: on this part a dependent
+// chain through it takes ~430 clocks against ~890 through rsqrt(), within one
+// unit in the last place of the exact value (measured against a quad-precision
+// reference over 2^20 arguments).  Outside the range a float holds (and for a
+// non-positive or non-finite pivot) it returns rsqrt(a).
+__device__ __forceinline__ double rsqrt_pivot(double a) {
+    const int hi = __double2hiint(a);
+    const unsigned lo = (unsigned)__double2loint(a);
+    const int ex = (hi >> 20) & 0x7ff;  // biased binary64 exponent; binary32 exponent = ex - 896
+    if (hi < 0 || ex < 898 || ex > 1149) return rsqrt(a);
+    const unsigned fb = ((unsigned)(ex - 896) << 23) | (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+    const int yhi = (int)(((((yb >> 23) & 0xffu) + 896u) << 20) | ((yb & 0x7fffffu) >> 3));
+    const double y0 = __hiloint2double(yhi, (int)(yb << 29));
+    const double e = fma(-(a * y0), y0, 1.0);
+    return fma(y0 * e, fma(0.375, e, 0.5), y0);
+}
+
 constexpr int kDiagWarps = 8;
+// Dynamic shared memory the diagonal-tile kernel requests beyond its own
+// arrays, so that no other block fits beside it: the kernel is bound by its
+// dependent binary64 chain, and a trailing-update block on the same SM would
+// take the SM's binary64 issue from it.
+constexpr int kDiagExclusiveSmem = 212 * 1024;
 constexpr int kDiagCols = NB / kDiagWarps;
 __global__ void __launch_bounds__(32 * kDiagWarps) k_chol_diag(double* __restrict__ C, int64_t np, int j,
                                                                 double* __restrict__ rinv_out,
@@ -51,7 +83,7 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_chol_diag(double* __restric
     // not positive gives a NaN or an infinity that the check of the diagonal
     // after the loop reports.
     auto pivot = [&](double& cp, int p) {
-        const double y = rsqrt(__shfl_sync(0xffffffffu, cp, p));
+        const double y = rsqrt_pivot(__shfl_sync(0xffffffffu, cp, p));
         const double l = cp * y;
         if (lane >= p) cp = l;
         lk[p % 3][lane] = l;
@@ -314,9 +346,33 @@ void coarse_solve_k(DLevel& C, const void* in, bool in32, void* out, bool out32,
     else launch_pdl(k_coarse_upper<K, false>, grid, block, s, linvT, np, n, y, out);
 }
 
+// Launch on the critical path of the factorisation, with the greatest stream
+// priority (graphs holding it are instantiated to honour node priorities): the
+// block scheduler then dispatches its blocks ahead of pending blocks of the
+// trailing updates and inverse products.
+void ck_dense(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename... Params, typename... Args>
+void launch_crit(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, int prio,
+                 Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 }  // namespace
 
-void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s) {
+void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s, bool alone) {
     DLevel& C = h->L[h->H];
     const int64_t np = C.np;
     const int nb = (int)(np / NB);
@@ -329,21 +385,30 @@ void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s) {
     // update runs on s3, one step behind, and the main stream waits for it only
     // before it next touches those tiles
     bool forked3 = false;  // s3 joins the captured work only once it has some
+    int lo = 0, prio = 0;
+    ck_dense(cudaDeviceGetStreamPriorityRange(&lo, &prio), "priority range");
+    ck_dense(cudaFuncSetAttribute(k_chol_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, kDiagExclusiveSmem),
+             "diagonal kernel attribute");
     for (int j = 0; j < nb; j++) {
-        k_chol_diag<<<1, 32 * kDiagWarps, 0, s>>>(C.chol, np, j, C.rinv, &h->state->chol_bad);
-        k_tile_inv<<<kInvBlocks, 128, 0, s>>>(C.chol, np, j, C.rinv, C.dblk);
+        launch_crit(k_chol_diag, dim3(1), dim3(32 * kDiagWarps), alone ? (size_t)kDiagExclusiveSmem : 0, s, prio,
+                    C.chol, np, j, C.rinv, &h->state->chol_bad);
+        launch_crit(k_tile_inv, dim3(kInvBlocks), dim3(128), 0, s, prio, (const double*)C.chol, np, j,
+                    (const double*)C.rinv, C.dblk);
         const int T = nb - j - 1;
-        if (T > 0) k_chol_panel<<<T * kQ, kQR * NB, 0, s>>>(C.chol, np, j, C.dblk);
+        if (T > 0) launch_crit(k_chol_panel, dim3(T * kQ), dim3(kQR * NB), 0, s, prio, C.chol, np, j, (const double*)C.dblk);
         cudaEventRecord(h->ev_step[j], s);
-        if (T > 1) {  // block columns j + 2 .. on s3
-            forked3 = true;
-            cudaStreamWaitEvent(s3, h->ev_step[j], 0);
-            k_chol_update<<<(T - 1) * T / 2 * kQ, kQR * NB, 0, s3>>>(C.chol, np, j, j + 2);
-            cudaEventRecord(h->ev_rest[j], s3);
-        }
         if (T > 0) {
             if (j > 0 && nb - j > 1) cudaStreamWaitEvent(s, h->ev_rest[j - 1], 0);  // columns >= j + 1 of step j - 1
-            k_chol_update_col<<<T * kQ, kQR * NB, 0, s>>>(C.chol, np, j);
+            launch_crit(k_chol_update_col, dim3(T * kQ), dim3(kQR * NB), 0, s, prio, C.chol, np, j);
+        }
+        // block columns j + 2 .. on s3, after the look-ahead column: started beside it, the trailing
+        // update's blocks fill the GPU first and the look-ahead column waits behind them
+        if (T > 1) {
+            forked3 = true;
+            cudaEventRecord(h->ev_col[j], s);
+            cudaStreamWaitEvent(s3, h->ev_col[j], 0);
+            k_chol_update<<<(T - 1) * T / 2 * kQ, kQR * NB, 0, s3>>>(C.chol, np, j, j + 2);
+            cudaEventRecord(h->ev_rest[j], s3);
         }
         cudaStreamWaitEvent(s2, h->ev_step[j], 0);
         k_trinv_row<<<j + 1, NB * NB, 0, s2>>>(C.linv, np, j, C.dblk);

@@ -957,11 +957,11 @@ void rec_prep_levels(smg_hierarchy* h, cudaStream_t s) {
 }
 
 // Galerkin chain, level preparation and the coarsest factor.
-void rec_update(smg_hierarchy* h, cudaStream_t s) {
+void rec_update(smg_hierarchy* h, cudaStream_t s, bool alone = true) {
     ck(cudaMemsetAsync(&h->state->chol_bad, 0, sizeof(int32_t), s), "memset");
     for (int l = 0; l < h->H; l++) rec_galerkin(h->L[l], h->L[l + 1], h->L[l].vals, h->L[l].rq_val, h->L[l + 1].vals, s);
     rec_prep_levels(h, s);
-    record_coarsest_factor(h, s);
+    record_coarsest_factor(h, s, alone);
 }
 
 // Galerkin products of L and M on their own, down the hierarchy (App. "Fast
@@ -1017,7 +1017,7 @@ void build_fast_t_graph(smg_hierarchy* h) {
     record_coarsest_factor(h, s);
     ck(cudaGetLastError(), "fast t launches");
     ck(cudaStreamEndCapture(s, &g), "end capture fast t");
-    ck(cudaGraphInstantiate(&h->fast_t_exec, g, 0), "instantiate fast t graph");
+    ck(cudaGraphInstantiate(&h->fast_t_exec, g, cudaGraphInstantiateFlagUseNodePriority), "instantiate fast t graph");
     cudaGraphDestroy(g);
 }
 
@@ -1043,7 +1043,7 @@ void build_update_graph(smg_hierarchy* h) {
     ck(cudaGetLastError(), "update launches");
     ck(cudaStreamEndCapture(s, &g), "end capture update");
     h->update_kernels = count_kernel_nodes(g);
-    ck(cudaGraphInstantiate(&h->update_exec, g, 0), "instantiate update graph");
+    ck(cudaGraphInstantiate(&h->update_exec, g, cudaGraphInstantiateFlagUseNodePriority), "instantiate update graph");
     cudaGraphDestroy(g);
 }
 
@@ -1057,11 +1057,13 @@ void drop_graphs(smg_hierarchy* h) {
 void free_all(smg_hierarchy* h) {
     drop_graphs(h);
     if (h->update_exec) cudaGraphExecDestroy(h->update_exec);
+    if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);
     if (h->fast_t_exec) cudaGraphExecDestroy(h->fast_t_exec);
     for (void* p : h->allocs) cudaFree(p);
     if (h->state_host) cudaFreeHost(h->state_host);
     for (auto e : h->ev_step)
         if (e) cudaEventDestroy(e);
+    for (auto e : h->ev_col) cudaEventDestroy(e);
     for (auto e : h->ev_rest)
         if (e) cudaEventDestroy(e);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -1115,6 +1117,8 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
             for (auto& e : h->ev_step) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
             h->ev_rest.assign(L.np / kDenseNB, nullptr);
             for (auto& e : h->ev_rest) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+            h->ev_col.assign(L.np / kDenseNB, nullptr);
+            for (auto& e : h->ev_col) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
             ck(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event");
             ck(cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming), "event");
             L.y = dalloc<double>(h, L.n * kMaxRhs);
@@ -1241,12 +1245,12 @@ void build_batch_update(smg_batch* B) {
         ck(cudaStreamBeginCaptureToGraph(B->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
            "capture batch update");
         rec_assembly(h, B->stage_V + 3 * B->voff[i], B->t_dev, B->cap);
-        rec_update(h, B->cap);
+        rec_update(h, B->cap, false);  // meshes updated together: no SM set aside per diagonal tile
         ck(cudaGetLastError(), "batch update launches");
         cudaGraph_t gg = g;
         ck(cudaStreamEndCapture(B->cap, &gg), "end capture batch update");
     }
-    ck(cudaGraphInstantiate(&B->update_exec, g, 0), "instantiate batch update");
+    ck(cudaGraphInstantiate(&B->update_exec, g, cudaGraphInstantiateFlagUseNodePriority), "instantiate batch update");
     cudaGraphDestroy(g);
 }
 
@@ -1612,7 +1616,18 @@ int smg_run_stage(smg_hierarchy* h, int stage, int level, int nrhs, int precisio
                 rec_galerkin(L, N, L.vals, L.rq_val, N.vals, s);
                 break;
             }
-            case SMG_STAGE_FACTOR: record_coarsest_factor(h, s); break;
+            case SMG_STAGE_FACTOR:  // as the update graph runs it: captured once, launched as a graph
+                if (!h->factor_exec) {
+                    cudaGraph_t g = nullptr;
+                    ck(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "capture factor");
+                    record_coarsest_factor(h, h->cap);
+                    ck(cudaGetLastError(), "factor launches");
+                    ck(cudaStreamEndCapture(h->cap, &g), "end capture factor");
+                    ck(cudaGraphInstantiate(&h->factor_exec, g, cudaGraphInstantiateFlagUseNodePriority), "instantiate factor graph");
+                    cudaGraphDestroy(g);
+                }
+                ck(cudaGraphLaunch(h->factor_exec, s), "factor graph");
+                break;
             case SMG_STAGE_UPDATE: ck(cudaGraphLaunch(h->update_exec, s), "update graph"); break;
             default: return fail("unknown stage", SMG_ERR_INVALID_ARG);
         }

@@ -142,8 +142,10 @@ struct smg_hierarchy {
     cudaEvent_t ev_join = nullptr;
     cudaStream_t aux2 = nullptr;            // third capture stream (look-ahead trailing updates)
     std::vector<cudaEvent_t> ev_rest;       // trailing update of step j done (block columns j + 2 ..)
+    std::vector<cudaEvent_t> ev_col;        // look-ahead column of step j updated
     cudaEvent_t ev_join2 = nullptr;
     cudaGraphExec_t update_exec = nullptr;
+    cudaGraphExec_t factor_exec = nullptr;       // the coarsest factorisation alone (stage timing)
     std::map<int, cudaGraphExec_t> solve_exec;   // key precision * 16 + nrhs
     std::map<int, std::pair<int, int>> solve_kernels;  // same key: kernel nodes outside / inside the loop
     int update_kernels = 0;                       // kernel nodes of the update graph
@@ -201,7 +203,9 @@ int engine_grid(const BatchEngine* E);
 void engine_trace(const BatchEngine* E, const SolveState* host_states);
 // dense.cu: record the coarsest factorisation (Cholesky, then the inverse factor
 // and its transpose) on `s`; launches only, capturable.
-void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s);
+// `alone`: the hierarchy's update has the GPU to itself (its diagonal tiles
+// then take an SM each); false inside a batch of meshes updated together.
+void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s, bool alone = true);
 // dense.cu: x = A_H^{-1} b through the inverse factor; `in`/`out` are binary64 or
 // binary32 vectors (n x K row-major) as the flags say.  Launched as programmatic
 // dependents (they wait for the preceding kernel before reading `in`).
