@@ -218,6 +218,10 @@ struct Dist {
 template <typename T>
 struct LevelCtx {
     const TailLevel<T>* L;
+    // the level's global arrays, read once at staging so that no per-step load
+    // goes through the level record in global memory first
+    const int32_t* gcol;
+    const T *gval, *gdinv, *gdiag;
     uint32_t tab;  // [n_my, E, cfirst[nc + 1], rows[nc], 6 * n_my]
     int n_my, nc, rlg, staged;
     uint32_t scol, sval, sdinv, sdiag;
@@ -293,6 +297,10 @@ __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const
     __syncthreads();
     LevelCtx<T> C;
     C.L = Lp;
+    C.gcol = L.col;
+    C.gval = L.sval;
+    C.gdinv = L.dinv;
+    C.gdiag = L.diag;
     C.tab = sm;
     C.n_my = lds_i(sm);
     const int E = lds_i(sm + 4u);
@@ -355,7 +363,8 @@ __device__ __forceinline__ LevelCtx<T> stage_level(const TailLevel<T>* Lp, const
 template <typename T, int K>
 struct TailRows {
     static constexpr int PRE = kTailPre;
-    uint32_t xa[PRE];  // local replica address of x at each entry's column
+    int cx[PRE];       // column of each entry (its x replica address is formed where x is read, so the
+                       // column loads of an unstaged level stay in flight across the step barrier)
     T v[PRE];
     T bb[K];
     T d;
@@ -368,11 +377,11 @@ struct TailRows {
 
     __device__ __forceinline__ int col_at(const LevelCtx<T>& C, int k) const {
         const int e = base + k * rstride + r;
-        return staged ? lds_i(C.scol + 4u * e) : __ldg(C.L->col + e);
+        return staged ? lds_i(C.scol + 4u * e) : __ldg(C.gcol + e);
     }
     __device__ __forceinline__ T val_at(const LevelCtx<T>& C, int k) const {
         const int e = base + k * rstride + r;
-        return staged ? lds<T>(C.sval + (uint32_t)sizeof(T) * e) : __ldg(C.L->sval + e);
+        return staged ? lds<T>(C.sval + (uint32_t)sizeof(T) * e) : __ldg(C.gval + e);
     }
 
     // work unit i (or none when i < 0); RESIDUAL: diagonal, else its reciprocal.
@@ -397,13 +406,12 @@ struct TailRows {
         for (int u = 0; u < PRE; u++) {
             const int k = sub + (u << rlg);
             if (k < W) {
-                const int c = col_at(C, k);
+                cx[u] = col_at(C, k);
                 v[u] = val_at(C, k);
-                xa[u] = C.xr + (uint32_t)(c * K * (int)sizeof(T));
             }
         }
         if (staged) d = lds<T>((RESIDUAL ? C.sdiag : C.sdinv) + (uint32_t)sizeof(T) * ((i << rl_lg) + r));
-        else d = RESIDUAL ? L.diag[row] : L.dinv[row];
+        else d = RESIDUAL ? C.gdiag[row] : C.gdinv[row];
         const uint32_t ba = C.bw + (uint32_t)((((i << rl_lg) + r) * K) * (int)sizeof(T));
 #pragma unroll
         for (int q = 0; q < K; q++) bb[q] = lds<T>(ba + q * (int)sizeof(T));
@@ -421,7 +429,7 @@ struct TailRows {
         for (int u = 0; u < PRE; u++)
             if (sub + (u << rlg) < W)
 #pragma unroll
-                for (int q = 0; q < K; q++) xv[u][q] = lds<T>(xa[u] + q * (int)sizeof(T));
+                for (int q = 0; q < K; q++) xv[u][q] = lds<T>(C.xr + (uint32_t)((cx[u] * K + q) * (int)sizeof(T)));
         // one chain per lane: every binary64 instruction holds the warp for the
         // same time whether or not it depends on the previous one, so fewer
         // instructions, not shorter chains, shorten a step; the row's first lane
@@ -483,20 +491,31 @@ __shared__ __align__(8) double tail_token[4];
 template <typename T, int K, class ColourOf>
 __device__ __forceinline__ void tail_relax(const LevelCtx<T>& C, const Dist& D, int steps, ColourOf col_of,
                                            int warp, int lane, StepBars& sb) {
-    TailRows<T, K> cur;
+    // Binary64 with one right-hand side: the warp's first two units of a step
+    // are both loaded before the preceding barrier (a colour class of a level
+    // above the staged sizes has up to ~2 units per warp at 8 warps per CTA);
+    // further units are loaded in the step.
+    constexpr bool TWO = sizeof(T) == 8 && K == 1;
+    constexpr int NW = TailThreads<T>::warps;
+    TailRows<T, K> cur, nxt;
     const uint32_t tok = (uint32_t)__cvta_generic_to_shared(tail_token);
-    auto load = [&](int c, int u) {
+    auto load = [&](TailRows<T, K>& t, int c, int u) {
         const int i = C.cfirst(c) + u;
-        cur.template load<false>(C, D, i < C.cfirst(c + 1) ? i : -1, lane);
+        t.template load<false>(C, D, i < C.cfirst(c + 1) ? i : -1, lane);
     };
-    if (steps > 0) load(col_of(0), warp);
+    auto load_step = [&](int c) {
+        load(cur, c, warp);
+        if (TWO) load(nxt, c, warp + NW);
+    };
+    if (steps > 0) load_step(col_of(0));
     for (int k = 0; k < steps; k++) {
         const int c = col_of(k);
         const int units = C.cfirst(c + 1) - C.cfirst(c);
         const uint32_t bar = sb.bar();
         cur.template run<false>(C, D, bar);
-        for (int u = warp + TailThreads<T>::warps; u < units; u += TailThreads<T>::warps) {
-            load(c, u);
+        if (TWO) nxt.template run<false>(C, D, bar);
+        for (int u = warp + (TWO ? 2 : 1) * NW; u < units; u += NW) {
+            load(cur, c, u);
             cur.template run<false>(C, D, bar);
         }
         if (warp == 0) {
@@ -506,7 +525,7 @@ __device__ __forceinline__ void tail_relax(const LevelCtx<T>& C, const Dist& D, 
                     st_async(dsm(tok + q * (uint32_t)sizeof(T), (uint32_t)lane), T(0), dsm(bar, (uint32_t)lane));
             if (lane == 0) mbar_arrive_expect_local(bar, (uint32_t)C.rows(c) * (uint32_t)(K * sizeof(T)));
         }
-        if (k + 1 < steps) load(col_of(k + 1), warp);
+        if (k + 1 < steps) load_step(col_of(k + 1));
         mbar_wait_cluster(bar, sb.parity(), C.L->err, sb.gave_up);
         sb.step++;
     }
