@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) gs_colour(co
     const int lane = threadIdx.x & 31;
     if (s >= s1) return;
     const SliceMeta m = slices[s];
-    RowSlice<T, K, R, Pre<T, K, R>::value> rs;
+    RowSlice<T, K, R, PreGS<T, K, R>::value> rs;
     rs.load(m, w % R, lane, col, sval);
     const bool valid = rs.r < m.nrows;
     const int row = m.row0 + (valid ? rs.r : 0);

@@ -45,6 +45,17 @@ template <typename T, int K, int R>
 struct Pre {
     static constexpr int value = R == 1 ? 6 : (R == 2 && K == 1) ? 12 : ((K <= 2 || sizeof(T) == 4) ? 8 : 4);
 };
+// The launched Gauss-Seidel colour step of a coarse level: a colour class
+// there fills fewer than one block per SM, so registers are not what limits
+// residency, while any entry past the prefetched ones costs a dependent load
+// after the wait that the whole step waits for.  Binary64 with one right-hand
+// side prefetches enough to cover rows of 36 (two lanes) and 44 (four lanes)
+// entries, the widest rows of the first coarse levels of the test meshes.
+template <typename T, int K, int R>
+struct PreGS {
+    static constexpr int value =
+        (sizeof(T) == 8 && K == 1 && R == 2) ? 18 : (sizeof(T) == 8 && K == 1 && R == 4) ? 11 : Pre<T, K, R>::value;
+};
 template <int K, int R>
 struct MinBlocks {
     static constexpr int value = (R == 1 && K == 1) ? 5 : 1;
