@@ -27,15 +27,6 @@ __global__ void k_pad_copy(const double* __restrict__ A, int64_t n, double* __re
     X[e] = (i == j) ? 1.0 : 0.0;
 }
 
-// Factor diagonal tile j.  A binary64 instruction holds its warp for about 64
-// clocks on this part (dependent or not), so the pivot chain (shuffle, CUDA's
-// binary64 rsqrt, scale) sets the time and everything else is kept off it:
-// warp w holds columns c = w, w + 8, ... of the tile in registers (lane = row);
-// in step k the owner of column k + 1 applies pivot k to that column only,
-// factors it (pivot k + 1) and publishes it in shared memory, while every other
-// warp applies pivot k to its columns right of k + 1 (lower triangle).  The
-// owner catches up on pivot k in step k + 1, so the published columns rotate
-// over three buffers and one barrier per pivot suffices.
 // Reciprocal square root on the pivot chain (a positive binary64 pivot): a
 // binary32 estimate y0 (the leading bits of a moved into a float by integer
 // operations, one rsqrtf), then one second-order correction from the binomial
@@ -59,6 +50,15 @@ __device__ __forceinline__ double rsqrt_pivot(double a) {
     return fma(y0 * e, fma(0.375, e, 0.5), y0);
 }
 
+// Factor diagonal tile j.  A binary64 instruction holds its warp for about 64
+// clocks on this part (dependent or not), so the pivot chain (shuffle,
+// rsqrt_pivot, scale) sets the time and everything else is kept off it:
+// warp w holds columns c = w, w + 8, ... of the tile in registers (lane = row);
+// in step k the owner of column k + 1 applies pivot k to that column only,
+// factors it (pivot k + 1) and publishes it in shared memory, while every other
+// warp applies pivot k to its columns right of k + 1 (lower triangle).  The
+// owner catches up on pivot k in step k + 1, so the published columns rotate
+// over three buffers and one barrier per pivot suffices.
 constexpr int kDiagWarps = 8;
 // Dynamic shared memory the diagonal-tile kernel requests beyond its own
 // arrays, so that no other block fits beside it: the kernel is bound by its
@@ -346,14 +346,14 @@ void coarse_solve_k(DLevel& C, const void* in, bool in32, void* out, bool out32,
     else launch_pdl(k_coarse_upper<K, false>, grid, block, s, linvT, np, n, y, out);
 }
 
-// Launch on the critical path of the factorisation, with the greatest stream
-// priority (graphs holding it are instantiated to honour node priorities): the
-// block scheduler then dispatches its blocks ahead of pending blocks of the
-// trailing updates and inverse products.
 void ck_dense(cudaError_t e, const char* what) {
     if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Launch on the critical path of the factorisation, with the greatest stream
+// priority (graphs holding it are instantiated to honour node priorities): the
+// block scheduler then dispatches its blocks ahead of pending blocks of the
+// trailing updates and inverse products.
 template <typename... Params, typename... Args>
 void launch_crit(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, int prio,
                  Args&&... args) {
@@ -367,7 +367,7 @@ void launch_crit(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, 
     attr[0].val.priority = prio;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    ck_dense(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...), "factor launch");
 }
 
 }  // namespace
@@ -395,7 +395,8 @@ void record_coarsest_factor(smg_hierarchy* h, cudaStream_t s, bool alone) {
         launch_crit(k_tile_inv, dim3(kInvBlocks), dim3(128), 0, s, prio, (const double*)C.chol, np, j,
                     (const double*)C.rinv, C.dblk);
         const int T = nb - j - 1;
-        if (T > 0) launch_crit(k_chol_panel, dim3(T * kQ), dim3(kQR * NB), 0, s, prio, C.chol, np, j, (const double*)C.dblk);
+        if (T > 0)
+            launch_crit(k_chol_panel, dim3(T * kQ), dim3(kQR * NB), 0, s, prio, C.chol, np, j, (const double*)C.dblk);
         cudaEventRecord(h->ev_step[j], s);
         if (T > 0) {
             if (j > 0 && nb - j > 1) cudaStreamWaitEvent(s, h->ev_rest[j - 1], 0);  // columns >= j + 1 of step j - 1
