@@ -206,6 +206,24 @@ def test_single_level_is_direct_solve():
     assert oracle.rel_residual(c.A, x.cpu().numpy(), b) <= 1e-13
 
 
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_dense_factor_direct_solve_many_tiles(nrhs):
+    """One level of 1,000 unknowns: the whole solve is the coarsest direct solve
+    through the blocked factor (32 tiles of 32, as the bench's coarsest level)
+    and its inverse, against a sparse LU solve."""
+    V, F = synth.torus(40, 25, seed=6)
+    c = Case(V, F, 1e-2, max_levels=1)
+    assert c.plan.num_levels == 1 and c.n == 1000
+    b = synth.uniform_rhs(c.n, nrhs=nrhs, seed=9)
+    x, info = c.h.solve(to_dev(b))
+    assert info["cycles"] == 1
+    xg = x.cpu().numpy()
+    assert oracle.rel_residual(c.A, xg, b) <= 1e-13
+    xs = spla.splu(c.A.tocsc()).solve(b)
+    assert maxrel(xg, xs) <= 1e-12
+    c.h.close()
+
+
 def test_mass_matches_oracle(disk):
     m = disk.h.mass().cpu().numpy()
     ref = oracle.lumped_mass(disk.V, disk.F)[disk.u]
