@@ -59,18 +59,21 @@ template <typename T>
 struct LevelView {
     const T *sval, *diag, *dinv, *p_w, *pt_w, *rq, *bval, *dblk;
     T *x, *b, *r;
+    const T* gsv;  // scaled SELL values and right-hand side of the Gauss-Seidel steps (binary64; null
+    T* bdi;        // for binary32, whose steps use sval, dinv and b)
 };
 
 template <typename T>
 LevelView<T> view(DLevel& L);
 template <>
 LevelView<double> view<double>(DLevel& L) {
-    return {L.vals + L.sbase, L.vals, L.dinv, L.p_w, L.pt_w, L.rq_val, L.b_val, L.b_dblk, L.x, L.b, L.r};
+    return {L.vals + L.sbase, L.vals, L.dinv, L.p_w, L.pt_w, L.rq_val, L.b_val, L.b_dblk, L.x, L.b, L.r, L.gsv,
+            L.bdi};
 }
 template <>
 LevelView<float> view<float>(DLevel& L) {
     return {L.vals32 + L.sbase, L.vals32, L.dinv32, L.p_w32, L.pt_w32, L.rq_val32, L.b_val32, L.b_dblk32, L.x32, L.b32,
-            L.r32};
+            L.r32, nullptr, nullptr};
 }
 
 // Dispatch on the lanes-per-row of a level (compile-time RR inside CALL).
@@ -115,6 +118,8 @@ void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse,
         return;
     }
     const bool bulk = R == 1 && (sizeof(T) == 4 ? L.bulk32 : L.bulk);
+    const T* gval = kern::ScaledGS<T>::value ? v.gsv : v.sval;  // binary64: rows scaled by 1 / a_ii
+    const T* grhs = kern::ScaledGS<T>::value ? v.bdi : b;
     for (int cc = first; cc < L.ncolours; cc++) {
         const int c = reverse ? L.ncolours - 1 - cc : cc;
         const int s0 = L.colour_slice[c], s1 = L.colour_slice[c + 1];
@@ -125,12 +130,12 @@ void rec_sweep(DLevel& L, const LevelView<T>& v, const T* b, T* x, bool reverse,
         if (bulk) {
             constexpr int WC = kBulkEntries;
             ck(launch_pdl_smem(kern::gs_colour_bulk<T, K, WC>, grid, block, (size_t)kern::BulkCfg<T, K, WC>::block_bytes,
-                               s, sl, s0, s1, col, v.sval, v.dinv, b, x, (int*)L.bulk_err),
+                               s, sl, s0, s1, col, gval, v.dinv, grhs, x, (int*)L.bulk_err),
                "staged gs launch");
             continue;
         }
-        SMG_R_SWITCH(R, ck(launch_pdl(kern::gs_colour<T, K, RR>, grid, block, s, sl, s0, s1, col, v.sval, v.dinv,
-                                        b, x), "gs launch"));
+        SMG_R_SWITCH(R, ck(launch_pdl(kern::gs_colour<T, K, RR>, grid, block, s, sl, s0, s1, col, gval, v.dinv,
+                                        grhs, x), "gs launch"));
     }
 }
 
@@ -185,8 +190,9 @@ void rec_restrict_fused(DLevel& L, const LevelView<T>& v, const LevelView<T>& vn
     const T* b = v.b;
     const T* x = v.x;
     const T* dinv_n = vn.dinv;
+    T* bdi_n = vn.bdi;  // binary64 levels swept on scaled rows also get b / a_ii
     SMG_R_SWITCH(R, ck(launch_pdl(kern::restrict_fused<T, K, RR>, grid, block, s, sl, L.rq_nslices, row, col, val, b,
-                                    x, vn.b, vn.x, dinv_n, nseed), "fused restriction launch"));
+                                    x, vn.b, vn.x, dinv_n, nseed, bdi_n), "fused restriction launch"));
 }
 
 // Shared-memory slots of the cluster tail: per level, the replica of x (n
@@ -360,7 +366,9 @@ void rec_pcg_iteration(smg_hierarchy* h, cudaStream_t s) {
     const int64_t n = L0.n, m = n * K;
     const dim3 eg(blocks_for(m)), blk(kern::kThreads), rg(kern::kNormBlocks);
     const double* r = h->cg_r;
-    ck(launch_pdl(kern::cg_precond_in<T>, eg, blk, s, m, r, v0.b, v0.x), "cg precond in");
+    const double* dinv0 = L0.dinv;
+    double* bdi0 = (double*)v0.bdi;
+    ck(launch_pdl(kern::cg_precond_in<T>, eg, blk, s, m, (int)K, r, v0.b, v0.x, dinv0, bdi0), "cg precond in");
     if (h->H == 0) record_coarsest_solve(h, K, v0.b, sizeof(T) == 4, v0.x, sizeof(T) == 4, s);
     else rec_vcycle<T, K>(h, s);
     const T* z = v0.x;
@@ -948,12 +956,26 @@ void rec_prep_levels(smg_hierarchy* h, cudaStream_t s) {
         kern::prep_level<<<blocks_for(L.nflat), kern::kThreads, 0, s>>>(L.nflat, L.n, L.vals, L.dinv, L.vals32,
                                                                       L.dinv32);
         kern::copy_f32<<<blocks_for(L.rq_nslots), kern::kThreads, 0, s>>>(L.rq_nslots, L.rq_val, L.rq_val32);
+        if (L.bs == 1)
+            kern::scale_sell<<<blocks_for((int64_t)L.nslices * 32), kern::kThreads, 0, s>>>(L.nslices, L.slices,
+                                                                                         L.vals + L.sbase, L.dinv, L.gsv);
         if (L.bs == 3) {
             const int64_t nb = 9 * L.b_nslots, nd = 9 * (L.n / 3);
             kern::block_gather<<<blocks_for(nb), kern::kThreads, 0, s>>>(nb, L.b_src, L.vals, L.b_val, L.b_val32);
             kern::block_gather<<<blocks_for(nd), kern::kThreads, 0, s>>>(nd, L.d_src, L.vals, L.b_dblk, L.b_dblk32);
         }
     }
+}
+
+// The caller's right-hand side into level 0's colour-major order, and b / a_ii
+// where level 0 is swept by binary64 Gauss-Seidel on scaled rows.
+void gather_rhs(smg_hierarchy* h, int K, const double* b, cudaStream_t s) {
+    DLevel& L0 = h->L[0];
+    const int64_t m = L0.n * K;
+    if (L0.bdi)
+        kern::gather_rows_scaled<<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, K, h->perm0, b, L0.dinv, L0.b, L0.bdi);
+    else
+        kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, K, h->perm0, b, L0.b);
 }
 
 // Galerkin chain, level preparation and the coarsest factor.
@@ -1147,6 +1169,9 @@ void create_impl(const Plan& P, const smg_options& o, smg_hierarchy* h) {
         }
         for (const SliceMeta& m : lp.slices) L.maxw = std::max(L.maxw, (int)m.width);
         L.dinv = dalloc<double>(h, L.n);
+        L.gsv = dalloc<double>(h, L.nflat - L.sbase);
+        L.bdi = dalloc<double>(h, L.n * kMaxRhs);
+        ck(cudaMemset(L.bdi, 0, sizeof(double) * L.n * kMaxRhs), "memset");
         L.vals32 = dalloc<float>(h, L.nflat);
         L.dinv32 = dalloc<float>(h, L.n);
         ck(cudaMemset(L.dinv, 0, sizeof(double) * L.n), "memset");
@@ -1266,7 +1291,7 @@ cudaGraphExec_t build_batch_solve(smg_batch* B, bool mixed) {
         double* xsrc = B->stage_x + B->uoff[i] * K;
         smg::SolveState* dst = B->states + i;
         auto pro = [&](cudaStream_t s) {
-            kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, K, h->perm0, bsrc, L0.b);
+            gather_rhs(h, K, bsrc, s);
             kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, K, h->perm0, xsrc, L0.x);
         };
         auto epi = [&](cudaStream_t s) {
@@ -1480,7 +1505,7 @@ int smg_solve_async(smg_hierarchy* h, const double* b, double* x, int nrhs, smg_
     const int64_t m = L0.n * nrhs;
     const bool mixed = h->opts.precision == SMG_MIXED;
     cudaGraphExec_t e = solve_graph(h, nrhs, mixed);
-    kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, b, L0.b);
+    gather_rhs(h, nrhs, b, s);
     kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, x, L0.x);
     ck(cudaGetLastError(), "gather");
     ck(cudaGraphLaunch(e, s), "solve graph");
@@ -1525,7 +1550,7 @@ int smg_vcycle(smg_hierarchy* h, const double* b, double* x, int nrhs, smg_strea
     DLevel& L0 = h->L[0];
     const int64_t m = L0.n * nrhs;
     cudaGraphExec_t e = cycle_graph(h, nrhs, false);
-    kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, b, L0.b);
+    gather_rhs(h, nrhs, b, s);
     kern::gather_rows<double><<<blocks_for(m), kern::kThreads, 0, s>>>(L0.n, nrhs, h->perm0, x, L0.x);
     ck(cudaGetLastError(), "gather");
     ck(cudaGraphLaunch(e, s), "vcycle graph");

@@ -90,6 +90,8 @@ struct DLevel {
     int64_t g_nnz = 0, q_nnz = 0;
     // vectors, capacity n * kMaxRhs
     double *x = nullptr, *b = nullptr, *r = nullptr;
+    double* bdi = nullptr;  // b_i / a_ii (binary64 Gauss-Seidel on scaled rows), n x kMaxRhs
+    double* gsv = nullptr;  // SELL values a_ij / a_ii (binary64 Gauss-Seidel on scaled rows)
     float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
     // coarsest: padded dense factor, its inverse and the inverse transposed
     int64_t np = 0;

@@ -49,6 +49,18 @@ __device__ __forceinline__ bool mbar_wait_cta(uint32_t bar, uint32_t parity, int
 }
 constexpr int kBulkWaitPolls = 1 << 22;  // far beyond any copy of a few KB; each poll may suspend the thread
 
+// Binary64 Gauss-Seidel runs on the operator with each row scaled by its
+// reciprocal diagonal (values a_ij / a_ii, right-hand side b_i / a_ii, both
+// formed outside the colour steps: the values at each update, b / a_ii where b
+// is written), so a row's update x_i = b_i / a_ii - sum_{j != i} (a_ij / a_ii) x_j
+// is one FMA chain without the final product by the reciprocal diagonal: that
+// product sat on the dependent chain of every colour step.  Binary32 keeps the
+// unscaled form.
+template <typename T>
+struct ScaledGS {
+    static constexpr bool value = sizeof(T) == 8;
+};
+
 // ---------------------------------------------------------------------------
 // Multicolour Gauss-Seidel (App. "Multi-Color Gauss Seidel"): one colour class,
 // x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii for every row i of the class.
@@ -69,16 +81,16 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) gs_colour(co
     rs.load(m, w % R, lane, col, sval);
     const bool valid = rs.r < m.nrows;
     const int row = m.row0 + (valid ? rs.r : 0);
-    const T d = dinv[row];
+    const T d = ScaledGS<T>::value ? T(1) : dinv[row];
     pdl_wait();
     pdl_trigger();
     T bv[K], acc[K];
 #pragma unroll
     for (int q = 0; q < K; q++) bv[q] = b[(int64_t)row * K + q];
-    rs.dot_from(m, col, sval, x, bv, acc);  // b_i - sum_{j != i} a_ij x_j
+    rs.dot_from(m, col, sval, x, bv, acc);  // b_i - sum_{j != i} a_ij x_j (scaled rows: the new x_i)
     if (valid && rs.sub == 0)
 #pragma unroll
-        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = acc[q] * d;
+        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = ScaledGS<T>::value ? acc[q] : acc[q] * d;
 }
 
 // One lane per row with the slice's entries staged by TMA: the form of
@@ -89,8 +101,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<K, R>::value) gs_colour(co
 // held in registers across the wait, so eight 256-thread blocks stay resident
 // per SM and a ~250k-row class is in flight in one wave, where the
 // register-prefetching kernel (five blocks per SM) runs it in two.  The
-// arithmetic is that of gs_colour<T, K, 1>: one FMA chain from b in slot order,
-// then the product with the reciprocal diagonal.  Entries past WC (rare wide
+// arithmetic is that of gs_colour<T, K, 1>: one FMA chain from b in slot order
+// (binary32: then the product with the reciprocal diagonal).  Entries past WC (rare wide
 // rows) are read from global memory.  A copy that never completes leaves the
 // warp after kBulkWaitPolls polls with *err set and its rows unchanged.
 template <typename T, int K, int WC>
@@ -125,7 +137,7 @@ __global__ void __launch_bounds__(kThreads, (BulkCfg<T, K, WC>::min_blocks))
     __syncwarp();
     const bool valid = lane < m.nrows;
     const int row = m.row0 + (valid ? lane : 0);
-    const T d = dinv[row];
+    const T d = ScaledGS<T>::value ? T(1) : dinv[row];
     pdl_wait();
     pdl_trigger();
     T acc[K];
@@ -159,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, (BulkCfg<T, K, WC>::min_blocks))
     }
     if (valid)
 #pragma unroll
-        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = acc[q] * d;
+        for (int q = 0; q < K; q++) x[(int64_t)row * K + q] = ScaledGS<T>::value ? acc[q] : acc[q] * d;
 }
 
 // 3|V| systems: one launch class (a vertex colour class) of the sweep in 3 x 3
@@ -321,7 +333,8 @@ __global__ void __launch_bounds__(kThreads) restrict_fused(const RQSlice* __rest
                                                            const int32_t* __restrict__ col, const T* __restrict__ val,
                                                            const T* __restrict__ b, const T* __restrict__ x,
                                                            T* __restrict__ bc, T* __restrict__ xc,
-                                                           const T* __restrict__ dinv_c, int nseed) {
+                                                           const T* __restrict__ dinv_c, int nseed,
+                                                           T* __restrict__ bdi_c) {
     constexpr int RL = 32 / R, PRE = 8;
     const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int s = w / R;
@@ -343,7 +356,7 @@ __global__ void __launch_bounds__(kThreads) restrict_fused(const RQSlice* __rest
             v[u] = ldg(val + m.off + k * 32 + r);
         }
     }
-    const T dseed = (valid && I < nseed) ? dinv_c[I] : T(0);
+    const T dc = (valid && (I < nseed || bdi_c != nullptr)) ? dinv_c[I] : T(0);
     pdl_wait();
     pdl_trigger();
     T acc[K];
@@ -379,7 +392,8 @@ __global__ void __launch_bounds__(kThreads) restrict_fused(const RQSlice* __rest
 #pragma unroll
         for (int q = 0; q < K; q++) {
             bc[(int64_t)I * K + q] = acc[q];
-            xc[(int64_t)I * K + q] = I < nseed ? acc[q] * dseed : T(0);
+            if (bdi_c) bdi_c[(int64_t)I * K + q] = acc[q] * dc;
+            xc[(int64_t)I * K + q] = I < nseed ? acc[q] * dc : T(0);
         }
 }
 
@@ -643,15 +657,18 @@ __global__ void cg_copy(int64_t m, const double* __restrict__ src, double* __res
     dst[e] = src[e];
 }
 
-// Right-hand side and zero start of the preconditioner cycle: b_0 <- r, x_0 <- 0.
+// Right-hand side and zero start of the preconditioner cycle: b_0 <- r, x_0 <- 0
+// (and, for a binary64 cycle, b_0 / a_ii into bdi0 when given; K columns).
 template <typename T>
-__global__ void cg_precond_in(int64_t m, const double* __restrict__ r, T* __restrict__ b0, T* __restrict__ x0) {
+__global__ void cg_precond_in(int64_t m, int K, const double* __restrict__ r, T* __restrict__ b0, T* __restrict__ x0,
+                              const double* __restrict__ dinv0, double* __restrict__ bdi0) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m) return;
     pdl_wait();
     pdl_trigger();
     b0[e] = (T)r[e];
     x0[e] = T(0);
+    if (bdi0) bdi0[e] = r[e] * dinv0[e / K];
 }
 
 // Partials of rho = r . z per column (z in the cycle's precision).
@@ -971,6 +988,21 @@ __global__ void prep_level(int64_t nflat, int64_t n, const double* __restrict__ 
     }
 }
 
+// Off-diagonal SELL values scaled by their row's reciprocal diagonal (one warp
+// per slice, lane = row of the slice; padding rows hold zeros).
+__global__ void scale_sell(int nslices, const SliceMeta* __restrict__ slices, const double* __restrict__ sval,
+                           const double* __restrict__ dinv, double* __restrict__ out) {
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= nslices) return;
+    const SliceMeta m = slices[w];
+    const double d = lane < m.nrows ? dinv[m.row0 + lane] : 0.0;
+    for (int k = 0; k < m.width; k++) {
+        const int64_t e = (int64_t)m.off + k * 32 + lane;
+        out[e] = sval[e] * d;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Permutation between the caller's unknown order and the colour-major order.
 template <typename T>
@@ -980,6 +1012,18 @@ __global__ void gather_rows(int64_t n, int K, const int32_t* __restrict__ perm, 
     if (e >= n * K) return;
     const int64_t p = e / K, q = e - p * K;
     dst[e] = src[(int64_t)perm[p] * K + q];
+}
+// The same for the level-0 right-hand side, also writing b_i / a_ii (binary64
+// Gauss-Seidel's scaled rows).
+__global__ void gather_rows_scaled(int64_t n, int K, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                                   const double* __restrict__ dinv, double* __restrict__ dst,
+                                   double* __restrict__ dst_scaled) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * K) return;
+    const int64_t p = e / K, q = e - p * K;
+    const double v = src[(int64_t)perm[p] * K + q];
+    dst[e] = v;
+    dst_scaled[e] = v * dinv[p];
 }
 template <typename T>
 __global__ void scatter_rows(int64_t n, int K, const int32_t* __restrict__ perm, const T* __restrict__ src,
