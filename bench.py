@@ -54,15 +54,15 @@ L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic of the level-0 sweep from one ncu capture: dram__bytes_read.sum
 # + dram__bytes_write.sum of the level-0 binary64 colour launches, per sweep
-# (4 classes x 28.13 MB).  Valid only for the kernel source it was taken on;
+# (4 classes x 26.13 MB).  Valid only for the kernel source it was taken on;
 # reported as null otherwise.
-TRAFFIC_CAPTURE = dict(bytes_per_sweep=28134144 + 28132608 + 28132864 + 28132864, bytes_per_launch=28.13e6,
+TRAFFIC_CAPTURE = dict(bytes_per_sweep=26133760 + 26132224 + 26132224 + 26131712, bytes_per_launch=26.13e6,
                        regions=(("paper_2104_13755_gb300/csrc/rowslice.cuh", "constexpr int kThreads = 256;",
                                  "}  // namespace kern"),
                                 ("paper_2104_13755_gb300/csrc/kernels.cuh",
                                  "// ---------------------------------------------------------------------------\n"
                                  "// Multicolour Gauss-Seidel", "// Damped Jacobi update")),
-                       sha256="43e759511d63ecfd037b2777ca019c3ca9e1d31a03501096dc86fa883e58ca19")
+                       sha256="35b591d3ff2b32291b12b0779e6ca50e24e0f94b60bcff874f275247a098eaa9")
 
 
 def captured_traffic():
@@ -90,8 +90,8 @@ def captured_traffic():
 # of one plain cycle graph, caches kept warm between kernels as in a solve).
 # Valid only while the kernel and layout sources are the ones captured (a hash
 # over the CUDA and plan sources); null otherwise or before a capture exists.
-CYCLE_TRAFFIC = dict(bytes_per_cycle=662636800 + 50618880,
-                     sha256="8f190aecd5d0ec5e43f6f7be139cac30035f31e41f5b7b9dbd9f6518c6f117f5")
+CYCLE_TRAFFIC = dict(bytes_per_cycle=608224512 + 52605696,
+                     sha256="8369f61993066303f38a6be9841634c8a90fc41adeffb43d68b59044c1c5ae8d")
 CYCLE_SOURCES = ("kernels.cuh", "rowslice.cuh", "tail.cuh", "dense.cu", "device.cu", "device.hpp", "plan.hpp",
                  "plan.cpp")
 
